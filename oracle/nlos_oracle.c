@@ -1,0 +1,489 @@
+/*
+ * FP64 CPU oracle for the NLOS intensity-transport transient simulator
+ * (arXiv 2506.03747). TEST INFRASTRUCTURE ONLY: the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg use it; the product path never
+ * does. It shares no code with the CUDA library.
+ *
+ * Everything here is the plain definition, evaluated brute force over all
+ * (scan point, surface point) pairs, in double precision, with no blocking,
+ * fusion or reordering beyond what the definition states. OpenMP only splits
+ * independent scan points (or surface points, for the gradient) over threads.
+ *
+ * Readings of the paper taken here (each restated where it is used):
+ *  - c = 299 792 458 m/s (the paper does not state it).
+ *  - Scan and surface grids are cell-centred.
+ *  - Stand-off: the laser/SPAD optics sit at D = (0, 0, standoff) in front of
+ *    the wall centre; the two device legs |D - l_s| + |d_s - D| are part of the
+ *    path (or 2*standoff when the constant mode is chosen).
+ *  - The acquisition window starts at path length L0 (default: the device legs
+ *    of the wall centre, so t = 0 is the first bounce at the wall centre, the
+ *    convention of Eq. 1).
+ *  - Bin b holds u in [b, b+1); pairs with u < 0 or u >= B are dropped.
+ *  - Object-side cosines are clamped at zero (back-facing patches give no
+ *    light); no other factor is clamped; no visibility test (Eq. 1 has none).
+ *  - Jitter taps are normalised to sum 1 and the trace is zero-padded.
+ *  - Noise follows Algorithm 1: blur first, then Poisson.
+ */
+#include "nlos_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* ---------------------------------------------------------------------------
+ * Scan geometry.
+ * The wall scan is an N_x x N_y grid of spots over [-w_x, w_x] x [-w_y, w_y]
+ * (w is the half side of the scanned area, the paper's "w" in Eq. 8). The
+ * paper's normalised grid (Eq. 5/6) includes the end points because it serves
+ * the padded LCT volume; here each spot sits at the centre of its cell.
+ * ------------------------------------------------------------------------- */
+void orc_scan_geometry(const orc_geom* g, int64_t s, double l[3], double d[3], double* legs) {
+  int64_t ix = s % g->scan_nx;
+  int64_t iy = s / g->scan_nx;
+  double x = -g->wall_half_x + ((double)ix + 0.5) * (2.0 * g->wall_half_x / (double)g->scan_nx);
+  double y = -g->wall_half_y + ((double)iy + 0.5) * (2.0 * g->wall_half_y / (double)g->scan_ny);
+  d[0] = x; d[1] = y; d[2] = 0.0;
+  if (g->nonconfocal) {
+    l[0] = g->laser_x; l[1] = g->laser_y; l[2] = 0.0;
+  } else {
+    l[0] = x; l[1] = y; l[2] = 0.0;
+  }
+  if (g->standoff_mode == 1) {
+    *legs = 2.0 * g->standoff;
+  } else {
+    /* device point D = (0, 0, standoff): leg D -> l_s plus leg d_s -> D */
+    double a = sqrt(l[0] * l[0] + l[1] * l[1] + g->standoff * g->standoff);
+    double b = sqrt(d[0] * d[0] + d[1] * d[1] + g->standoff * g->standoff);
+    *legs = a + b;
+  }
+}
+
+/* Window start L0: explicit, or the device legs of the wall centre (2*standoff). */
+double orc_window_start(const orc_geom* g) {
+  if (isnan(g->window_start_m)) return 2.0 * g->standoff;
+  return g->window_start_m;
+}
+
+/* ---------------------------------------------------------------------------
+ * One pair (Eq. 1, generalised). The paper's integrand for a confocal scan is
+ * rho / r^4 placed at time 2r/c. For a surface sample p with albedo rho_p and
+ * patch area a_p, seen from laser spot l and detector spot d:
+ *   path   L = legs(s) + |x - l| + |x - d|
+ *   bin    u = (L - L0) / (c * dt)
+ *   weight w = rho_p * a_p * C / (|x - l|^2 |x - d|^2)
+ * with C = 1 (Eq. 1 as printed; gives rho/r^4 when l = d),
+ *      C = max(0, cos_l) max(0, cos_d) (Lambertian object, default),
+ *      C = the above times the two wall-side cosines (x - l)_z/|x - l| and
+ *          (x - d)_z/|x - d|,
+ * where cos_l = n . (l - x) / |l - x|, cos_d = n . (d - x) / |d - x|.
+ * ------------------------------------------------------------------------- */
+static void pair_at(const orc_geom* g, const double l[3], const double d[3], double legs,
+                    double L0, const double* pt, double* u, double* w) {
+  double vl[3] = {pt[0] - l[0], pt[1] - l[1], pt[2] - l[2]};
+  double vd[3] = {pt[0] - d[0], pt[1] - d[1], pt[2] - d[2]};
+  double rl = sqrt(vl[0] * vl[0] + vl[1] * vl[1] + vl[2] * vl[2]);
+  double rd = sqrt(vd[0] * vd[0] + vd[1] * vd[1] + vd[2] * vd[2]);
+  double L = legs + rl + rd;
+  *u = (L - L0) / (ORC_LIGHT_SPEED * g->bin_width_s);
+  double q = pt[6] * pt[7];
+  double C = 1.0;
+  if (g->cos_mode >= 1) {
+    double cl = -(pt[3] * vl[0] + pt[4] * vl[1] + pt[5] * vl[2]) / rl;
+    double cd = -(pt[3] * vd[0] + pt[4] * vd[1] + pt[5] * vd[2]) / rd;
+    C = (cl > 0.0 ? cl : 0.0) * (cd > 0.0 ? cd : 0.0);
+    if (g->cos_mode == 2) C *= (vl[2] / rl) * (vd[2] / rd);
+  }
+  *w = q * C / (rl * rl * rd * rd);
+}
+
+void orc_pair(const orc_geom* g, int64_t s, const double* pt, double* u, double* w) {
+  double l[3], d[3], legs;
+  orc_scan_geometry(g, s, l, d, &legs);
+  pair_at(g, l, d, legs, orc_window_start(g), pt, u, w);
+}
+
+/* ---------------------------------------------------------------------------
+ * Binned forward: tau[s][b] = sum of w over pairs with floor(u) = b, 0 <= b < B.
+ * Optional outputs for the parity rule of the tests:
+ *   flip_mass[s][b]: sum of w over pairs whose u lies within eps of an edge of
+ *                    bin b (such a pair may legitimately land on either side in
+ *                    a lower-precision evaluation);
+ *   edge_mass[s]:    the part of that mass at the window edges u = 0 and u = B;
+ *   n_boundary:      the number of pairs within eps of any bin edge 0..B.
+ * ------------------------------------------------------------------------- */
+int orc_forward_binned(const orc_geom* g, int64_t num_points, const double* pts,
+                       int64_t s_begin, int64_t s_count, double* tau,
+                       double eps, double* flip_mass, double* edge_mass,
+                       int64_t* n_boundary, int num_threads) {
+  const int32_t B = g->num_bins;
+  const double L0 = orc_window_start(g);
+  int64_t nb_total = 0;
+  memset(tau, 0, sizeof(double) * (size_t)s_count * (size_t)B);
+  if (flip_mass) memset(flip_mass, 0, sizeof(double) * (size_t)s_count * (size_t)B);
+  if (edge_mass) memset(edge_mass, 0, sizeof(double) * (size_t)s_count);
+#ifdef _OPENMP
+  if (num_threads <= 0) num_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(num_threads) reduction(+ : nb_total)
+#endif
+  for (int64_t i = 0; i < s_count; ++i) {
+    double l[3], d[3], legs;
+    orc_scan_geometry(g, s_begin + i, l, d, &legs);
+    double* row = tau + i * B;
+    for (int64_t p = 0; p < num_points; ++p) {
+      double u, w;
+      pair_at(g, l, d, legs, L0, pts + 8 * p, &u, &w);
+      if (u >= 0.0 && u < (double)B) row[(int64_t)floor(u)] += w;
+      if (eps > 0.0) {
+        double m = floor(u + 0.5);
+        if (fabs(u - m) < eps && m >= 0.0 && m <= (double)B) {
+          int64_t mi = (int64_t)m;
+          nb_total += 1;
+          if (flip_mass) {
+            if (mi >= 1) flip_mass[i * B + mi - 1] += w;
+            if (mi < B) flip_mass[i * B + mi] += w;
+          }
+          if (edge_mass && (mi == 0 || mi == B)) edge_mass[i] += w;
+        }
+      }
+    }
+  }
+  if (n_boundary) *n_boundary = nb_total;
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Gaussian timing jitter (Eq. 16/17, Algorithm 1 step 2.3).
+ * sigma = FWHM / (2 sqrt(2 ln 2)) expressed in bins, kernel length
+ * k = 2 ceil(2 sigma) + 1, taps exp(-j^2 / (2 sigma^2)) normalised to sum 1.
+ * FWHM = 0 gives the identity (k = 1). Returns k, or -k if max_taps < k.
+ * ------------------------------------------------------------------------- */
+int orc_jitter_taps(double fwhm_s, double bin_width_s, double* taps, int max_taps) {
+  if (!(fwhm_s > 0.0)) {
+    if (max_taps < 1) return -1;
+    taps[0] = 1.0;
+    return 1;
+  }
+  double sigma = fwhm_s / (2.0 * sqrt(2.0 * log(2.0)) * bin_width_s);
+  int R = (int)ceil(2.0 * sigma);
+  int k = 2 * R + 1;
+  if (k > max_taps) return -k;
+  double sum = 0.0;
+  for (int j = -R; j <= R; ++j) {
+    taps[j + R] = exp(-(double)j * (double)j / (2.0 * sigma * sigma));
+    sum += taps[j + R];
+  }
+  for (int j = 0; j < k; ++j) taps[j] /= sum;
+  return k;
+}
+
+/* out[s][b] = sum_j taps[j + R] * tau[s][b - j], j = -R..R, zero outside [0, B). */
+void orc_jitter(const double* tau, int64_t num_traces, int32_t num_bins,
+                const double* taps, int32_t k, double* out) {
+  int32_t R = (k - 1) / 2;
+  for (int64_t s = 0; s < num_traces; ++s) {
+    const double* in = tau + s * num_bins;
+    double* o = out + s * num_bins;
+    for (int32_t b = 0; b < num_bins; ++b) {
+      double acc = 0.0;
+      for (int32_t j = -R; j <= R; ++j) {
+        int32_t src = b - j;
+        if (src >= 0 && src < num_bins) acc += taps[j + R] * in[src];
+      }
+      o[b] = acc;
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10, from Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+ * as easy as 1, 2, 3" (SC'11). Each round multiplies words 0 and 2 of the
+ * counter by the two published multipliers, keeps the 64-bit products as
+ * (hi, lo) halves, and rebuilds the counter as
+ *   (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0);
+ * between rounds the key is bumped by the two published Weyl constants.
+ * ------------------------------------------------------------------------- */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += ORC_PHILOX_W0;
+      k1 += ORC_PHILOX_W1;
+    }
+    uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ---------------------------------------------------------------------------
+ * Per-bin random stream: key = (seed_lo, seed_hi), counter =
+ * (index_lo, index_hi, block, stream_tag), where index is the global bin index
+ * and block counts the 4-word blocks this bin has consumed. A word w maps to
+ * the uniform ((w >> 9) + 0.5) * 2^-23, which lies strictly inside (0, 1) and
+ * is exact in single precision.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  uint32_t key[2];
+  uint32_t ctr[4];
+  uint32_t buf[4];
+  int pos;
+} orc_stream;
+
+static void stream_init(orc_stream* st, uint64_t index, uint64_t seed, uint32_t stream_tag) {
+  st->key[0] = (uint32_t)seed;
+  st->key[1] = (uint32_t)(seed >> 32);
+  st->ctr[0] = (uint32_t)index;
+  st->ctr[1] = (uint32_t)(index >> 32);
+  st->ctr[2] = 0u;
+  st->ctr[3] = stream_tag;
+  orc_philox4x32_10(st->ctr, st->key, st->buf);
+  st->pos = 0;
+}
+
+static float stream_uniform(orc_stream* st) {
+  if (st->pos == 4) {
+    st->ctr[2] += 1u;
+    orc_philox4x32_10(st->ctr, st->key, st->buf);
+    st->pos = 0;
+  }
+  uint32_t w = st->buf[st->pos++];
+  return ((float)(w >> 9) + 0.5f) * 0x1p-23f;
+}
+
+/* ---------------------------------------------------------------------------
+ * Poisson sampling (Eq. 18/19). The sampled count decides an integer, so the
+ * sampler runs in single precision, the precision of the device kernel:
+ *  - lambda < 10: Knuth's multiplication method (multiply uniforms until the
+ *    product drops to exp(-lambda) or below; the count is the number of
+ *    factors minus one);
+ *  - lambda >= 10: PTRS, the transformed rejection method with squeeze of
+ *    W. Hoermann, "The transformed rejection method for generating Poisson
+ *    random variables", Insurance: Mathematics and Economics 12 (1993).
+ * Both loops are capped at 1000 steps (never reached in practice).
+ * lambda <= 0 or NaN gives 0.
+ * ------------------------------------------------------------------------- */
+static uint32_t poisson_knuth(float lam, orc_stream* st) {
+  float limit = expf(-lam);
+  float prod = 1.0f;
+  uint32_t k = 0;
+  for (int it = 0; it < 1000; ++it) {
+    prod *= stream_uniform(st);
+    if (prod <= limit) return k;
+    k += 1;
+  }
+  return k;
+}
+
+static uint32_t poisson_ptrs(float lam, orc_stream* st) {
+  float slam = sqrtf(lam);
+  float loglam = logf(lam);
+  float b = 0.931f + 2.53f * slam;
+  float a = -0.059f + 0.02483f * b;
+  float inv_alpha = 1.1239f + 1.1328f / (b - 3.4f);
+  float v_r = 0.9277f - 3.6224f / (b - 2.0f);
+  for (int it = 0; it < 1000; ++it) {
+    float U = stream_uniform(st) - 0.5f;
+    float V = stream_uniform(st);
+    float us = 0.5f - fabsf(U);
+    float kf = floorf((2.0f * a / us + b) * U + lam + 0.43f);
+    if (us >= 0.07f && V <= v_r) return (uint32_t)kf;
+    if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+    float lhs = logf(V) + logf(inv_alpha) - logf(a / (us * us) + b);
+    float rhs = -lam + kf * loglam - lgammaf(kf + 1.0f);
+    if (lhs <= rhs) return (uint32_t)kf;
+  }
+  return (uint32_t)floorf(lam);
+}
+
+uint32_t orc_poisson_one(float lam, uint64_t index, uint64_t seed, uint32_t stream_tag) {
+  if (!(lam > 0.0f)) return 0u;
+  orc_stream st;
+  stream_init(&st, index, seed, stream_tag);
+  return lam < 10.0f ? poisson_knuth(lam, &st) : poisson_ptrs(lam, &st);
+}
+
+void orc_poisson(const float* lam, int64_t n, uint64_t index_base, uint64_t seed,
+                 uint32_t stream_tag, uint32_t* counts, int num_threads) {
+#ifdef _OPENMP
+  if (num_threads <= 0) num_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(static) num_threads(num_threads)
+#endif
+  for (int64_t i = 0; i < n; ++i)
+    counts[i] = orc_poisson_one(lam[i], index_base + (uint64_t)i, seed, stream_tag);
+}
+
+/* ---------------------------------------------------------------------------
+ * Differentiable splat (not in the paper, which bins and then blurs): each
+ * pair spreads its weight over the bins with a Gaussian of the jitter's sigma,
+ *   tau[s][b] = sum_p w_sp * phi(b + 1/2 - u_sp),
+ *   phi(x) = exp(-x^2 / (2 sigma^2)) / (sigma sqrt(2 pi)),  |x| < 6 sigma,
+ * over bins 0 <= b < B only.
+ * ------------------------------------------------------------------------- */
+static double splat_kernel(double x, double sigma) {
+  return exp(-x * x / (2.0 * sigma * sigma)) / (sigma * sqrt(2.0 * ORC_PI));
+}
+
+int orc_forward_splat(const orc_geom* g, double sigma_bins, int64_t num_points,
+                      const double* pts, int64_t s_begin, int64_t s_count,
+                      double* tau, int num_threads) {
+  const int32_t B = g->num_bins;
+  const double L0 = orc_window_start(g);
+  const double reach = 6.0 * sigma_bins;
+  memset(tau, 0, sizeof(double) * (size_t)s_count * (size_t)B);
+#ifdef _OPENMP
+  if (num_threads <= 0) num_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(num_threads)
+#endif
+  for (int64_t i = 0; i < s_count; ++i) {
+    double l[3], d[3], legs;
+    orc_scan_geometry(g, s_begin + i, l, d, &legs);
+    double* row = tau + i * B;
+    for (int64_t p = 0; p < num_points; ++p) {
+      double u, w;
+      pair_at(g, l, d, legs, L0, pts + 8 * p, &u, &w);
+      /* bins with |b + 1/2 - u| < 6 sigma */
+      int64_t b_lo = (int64_t)floor(u - 0.5 - reach);
+      int64_t b_hi = (int64_t)ceil(u - 0.5 + reach);
+      if (b_lo < 0) b_lo = 0;
+      if (b_hi > B - 1) b_hi = B - 1;
+      for (int64_t b = b_lo; b <= b_hi; ++b) {
+        double x = (double)b + 0.5 - u;
+        if (fabs(x) < reach) row[b] += w * splat_kernel(x, sigma_bins);
+      }
+    }
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Analytic gradient of a loss whose gradient with respect to tau is grad_tau
+ * ([S][B], all scan points), through the splat forward above, with respect to
+ *   grad_albedo[p] = dL/d rho_p,
+ *   grad_depth[p]  = dL/d delta_p at delta = 0, for the displaced point
+ *                    x_p + delta * n_p (normal and patch area held fixed).
+ * Per pair, with x_b = b + 1/2 - u and phi' = -(x / sigma^2) phi:
+ *   G0 = sum_b g[b] phi(x_b),  G1 = sum_b g[b] (x_b / sigma^2) phi(x_b),
+ *   dL/d rho   += (dw/d rho) G0,
+ *   dL/d delta += (dw/d delta) G0 + w (du/d delta) G1.
+ * Leg derivatives (x -> x + delta n):
+ *   dr/d delta = -cos,  d cos/d delta = -(1 - cos^2)/r,
+ *   d(z/r)/d delta = (n_z + (z/r) cos)/r,  du/d delta = -(cos_l + cos_d)/(c dt).
+ * ------------------------------------------------------------------------- */
+static void leg_factor(int cos_mode, const double* pt, const double v[3], double r,
+                       double* F, double* dF) {
+  double ndotv = pt[3] * v[0] + pt[4] * v[1] + pt[5] * v[2];
+  double c = -ndotv / r;                 /* cosine at the object */
+  double dc = -(1.0 - c * c) / r;        /* its delta-derivative */
+  double dr = -c;                        /* d r / d delta */
+  double fc = 1.0, dfc = 0.0;            /* cosine factor */
+  if (cos_mode >= 1) {
+    if (c > 0.0) { fc = c; dfc = dc; } else { fc = 0.0; dfc = 0.0; }
+  }
+  double fw = 1.0, dfw = 0.0;            /* wall-side cosine factor */
+  if (cos_mode == 2) {
+    fw = v[2] / r;
+    dfw = (pt[5] + fw * c) / r;
+  }
+  double inv_r2 = 1.0 / (r * r);
+  *F = fc * fw * inv_r2;
+  *dF = (dfc * fw + fc * dfw) * inv_r2 + fc * fw * (-2.0 * inv_r2 / r) * dr;
+}
+
+int orc_backward_splat(const orc_geom* g, double sigma_bins, int64_t num_points,
+                       const double* pts, const double* grad_tau,
+                       double* grad_albedo, double* grad_depth, int num_threads) {
+  const int32_t B = g->num_bins;
+  const int64_t S = (int64_t)g->scan_nx * (int64_t)g->scan_ny;
+  const double L0 = orc_window_start(g);
+  const double cdt = ORC_LIGHT_SPEED * g->bin_width_s;
+  const double reach = 6.0 * sigma_bins;
+  const double s2 = sigma_bins * sigma_bins;
+#ifdef _OPENMP
+  if (num_threads <= 0) num_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 64) num_threads(num_threads)
+#endif
+  for (int64_t p = 0; p < num_points; ++p) {
+    const double* pt = pts + 8 * p;
+    double ga = 0.0, gd = 0.0;
+    for (int64_t s = 0; s < S; ++s) {
+      double l[3], d[3], legs;
+      orc_scan_geometry(g, s, l, d, &legs);
+      double vl[3] = {pt[0] - l[0], pt[1] - l[1], pt[2] - l[2]};
+      double vd[3] = {pt[0] - d[0], pt[1] - d[1], pt[2] - d[2]};
+      double rl = sqrt(vl[0] * vl[0] + vl[1] * vl[1] + vl[2] * vl[2]);
+      double rd = sqrt(vd[0] * vd[0] + vd[1] * vd[1] + vd[2] * vd[2]);
+      double u = (legs + rl + rd - L0) / cdt;
+      double Fl, dFl, Fd, dFd;
+      leg_factor(g->cos_mode, pt, vl, rl, &Fl, &dFl);
+      leg_factor(g->cos_mode, pt, vd, rd, &Fd, &dFd);
+      double q = pt[6] * pt[7];
+      double w = q * Fl * Fd;
+      double dw_drho = pt[7] * Fl * Fd;
+      double dw_ddelta = q * (dFl * Fd + Fl * dFd);
+      double cl = -(pt[3] * vl[0] + pt[4] * vl[1] + pt[5] * vl[2]) / rl;
+      double cd = -(pt[3] * vd[0] + pt[4] * vd[1] + pt[5] * vd[2]) / rd;
+      double du_ddelta = -(cl + cd) / cdt;
+      int64_t b_lo = (int64_t)floor(u - 0.5 - reach);
+      int64_t b_hi = (int64_t)ceil(u - 0.5 + reach);
+      if (b_lo < 0) b_lo = 0;
+      if (b_hi > B - 1) b_hi = B - 1;
+      double G0 = 0.0, G1 = 0.0;
+      const double* grow = grad_tau + s * B;
+      for (int64_t b = b_lo; b <= b_hi; ++b) {
+        double x = (double)b + 0.5 - u;
+        if (fabs(x) < reach) {
+          double k = splat_kernel(x, sigma_bins);
+          G0 += grow[b] * k;
+          G1 += grow[b] * (x / s2) * k;
+        }
+      }
+      ga += dw_drho * G0;
+      gd += dw_ddelta * G0 + w * du_ddelta * G1;
+    }
+    grad_albedo[p] = ga;
+    grad_depth[p] = gd;
+  }
+  return 0;
+}
+
+/* Per-pair table for a list of scan points: u[i][p] and w[i][p] as in pair_at. */
+void orc_pair_table(const orc_geom* g, int64_t num_points, const double* pts,
+                    const int64_t* scan_ids, int64_t n_scan, double* u, double* w,
+                    int num_threads) {
+  const double L0 = orc_window_start(g);
+#ifdef _OPENMP
+  if (num_threads <= 0) num_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(num_threads)
+#endif
+  for (int64_t i = 0; i < n_scan; ++i) {
+    double l[3], d[3], legs;
+    orc_scan_geometry(g, scan_ids[i], l, d, &legs);
+    for (int64_t p = 0; p < num_points; ++p)
+      pair_at(g, l, d, legs, L0, pts + 8 * p, u + i * num_points + p, w + i * num_points + p);
+  }
+}
+
+/* Expected counts per bin in single precision, lambda = fmaf(scale, tau_G, dark)
+ * (one rounding), from the double tau_G rounded to float. */
+void orc_noise_lambda(const double* tau_g, int64_t n, float scale, float dark, float* lam) {
+  for (int64_t i = 0; i < n; ++i) lam[i] = fmaf(scale, (float)tau_g[i], dark);
+}
