@@ -271,13 +271,16 @@ static float stream_uniform(orc_stream* st) {
 
 /* ---------------------------------------------------------------------------
  * Poisson sampling (Eq. 18/19). The sampled count decides an integer, so the
- * sampler runs in single precision, the precision of the device kernel:
- *  - lambda < 10: Knuth's multiplication method (multiply uniforms until the
- *    product drops to exp(-lambda) or below; the count is the number of
- *    factors minus one);
+ * host and the device take each decision in the same precision: lambda is a
+ * single-precision value and the uniforms are exact in single precision;
+ *  - lambda < 10: Knuth's multiplication method in single precision (multiply
+ *    uniforms until the product drops to expf(-lambda) or below; the count is
+ *    the number of factors minus one);
  *  - lambda >= 10: PTRS, the transformed rejection method with squeeze of
  *    W. Hoermann, "The transformed rejection method for generating Poisson
- *    random variables", Insurance: Mathematics and Economics 12 (1993).
+ *    random variables", Insurance: Mathematics and Economics 12 (1993),
+ *    evaluated in double (log and lgamma of double agree to about the last
+ *    bit on host and device, where single-precision lgammaf does not).
  * Both loops are capped at 1000 steps (never reached in practice).
  * lambda <= 0 or NaN gives 0.
  * ------------------------------------------------------------------------- */
@@ -293,25 +296,26 @@ static uint32_t poisson_knuth(float lam, orc_stream* st) {
   return k;
 }
 
-static uint32_t poisson_ptrs(float lam, orc_stream* st) {
-  float slam = sqrtf(lam);
-  float loglam = logf(lam);
-  float b = 0.931f + 2.53f * slam;
-  float a = -0.059f + 0.02483f * b;
-  float inv_alpha = 1.1239f + 1.1328f / (b - 3.4f);
-  float v_r = 0.9277f - 3.6224f / (b - 2.0f);
+static uint32_t poisson_ptrs(float lam_f, orc_stream* st) {
+  double lam = (double)lam_f;
+  double slam = sqrt(lam);
+  double loglam = log(lam);
+  double b = 0.931 + 2.53 * slam;
+  double a = -0.059 + 0.02483 * b;
+  double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+  double v_r = 0.9277 - 3.6224 / (b - 2.0);
   for (int it = 0; it < 1000; ++it) {
-    float U = stream_uniform(st) - 0.5f;
-    float V = stream_uniform(st);
-    float us = 0.5f - fabsf(U);
-    float kf = floorf((2.0f * a / us + b) * U + lam + 0.43f);
-    if (us >= 0.07f && V <= v_r) return (uint32_t)kf;
-    if (kf < 0.0f || (us < 0.013f && V > us)) continue;
-    float lhs = logf(V) + logf(inv_alpha) - logf(a / (us * us) + b);
-    float rhs = -lam + kf * loglam - lgammaf(kf + 1.0f);
+    double U = (double)stream_uniform(st) - 0.5;
+    double V = (double)stream_uniform(st);
+    double us = 0.5 - fabs(U);
+    double kf = floor((2.0 * a / us + b) * U + lam + 0.43);
+    if (us >= 0.07 && V <= v_r) return (uint32_t)kf;
+    if (kf < 0.0 || (us < 0.013 && V > us)) continue;
+    double lhs = log(V) + log(inv_alpha) - log(a / (us * us) + b);
+    double rhs = -lam + kf * loglam - lgamma(kf + 1.0);
     if (lhs <= rhs) return (uint32_t)kf;
   }
-  return (uint32_t)floorf(lam);
+  return (uint32_t)floor(lam);
 }
 
 uint32_t orc_poisson_one(float lam, uint64_t index, uint64_t seed, uint32_t stream_tag) {
