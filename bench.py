@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 NLOS transient simulator.
+
+Metric: pair-interactions/s of the whole forward hot path (ingest/pack,
+pair histogram with fused jitter, FP64 energy reduction, Philox Poisson
+noise) on the 64x64-scan union-of-primitives workload (confocal, 2 m x 2 m,
+512 bins of 8 ps, 1 m stand-off, 262,144 surface points, 60 ps jitter,
+100-photon peak + 1e-3 dark counts), with inputs resident in HBM. One JSON
+line on rank 0; see --help.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank simulates its own independent scene (seed
+offset by the rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s vs FP32 roofline; served p50/p99 latency vs one-by-one"
+UNIT = "pairs/s"
+FP32_SLOTS_PER_PAIR = 17   # algorithmic FP32 issue slots per evaluated pair
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+WORKLOAD_DESC = ("union64: confocal 64x64 scan over 2 m x 2 m, 512 bins x 8 ps, stand-off 1 m "
+                 "(Euclidean legs), 262,144 area-uniform points on a seeded union of 3-6 "
+                 "spheres/boxes at 0.3-1.2 m, albedo U[0.2,1], jitter FWHM 60 ps, Poisson noise "
+                 "peak 100 photons + 1e-3 dark/bin")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(rank: int):
+    import scenes
+    params, pts = scenes.workload_union64(seed=scenes.SEED_BASE + 2 + 1000 * rank)
+    return params, pts
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    smax.append(float(c[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_for(kernel_file: str):
+    """DRAM bytes per forward launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "forward_union64_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    with open(kernel_file, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    return d.get("dram_bytes_per_launch") if d.get("forward_cu_sha256") == h else None
+
+
+def cpu_baseline(params, pts, scan_count: int):
+    """The FP64 oracle as it stands, on all host cores, on the first scan_count
+    scan points of the workload (forward + jitter + energy + noise)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.simulate(params, pts, 0, scan_count, threads=cores)
+    dt = time.perf_counter() - t0
+    pairs = scan_count * pts.shape[0]
+    return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"scan points 0..{scan_count - 1} of {params['scan_nx'] * params['scan_ny']}"
+                      f" x all {pts.shape[0]} points, one pass (FP64 forward + jitter + energy + "
+                      f"Poisson noise), {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    params, pts = _workload(0)
+    S = params["scan_nx"] * params["scan_ny"]
+    scan_count = 512  # bounded sample per step (1/8 of the scan)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.simulate(params, pts, 0, scan_count, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.simulate(params, pts, 0, scan_count, threads=cores)
+    dt = time.perf_counter() - t0
+    pairs = args.steps * scan_count * pts.shape[0]
+    v = pairs / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC,
+                                            "sample_per_step": f"{scan_count} of {S} scan points"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{scan_count} of {S} scan points x {pts.shape[0]} points "
+                                       "per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2506_03747_gb300 import build as nbuild
+    from paper_2506_03747_gb300 import nlos
+    nbuild.build()
+    nlos.load()
+
+    params, pts_np = _workload(rank)
+    prm = nlos.params(params)
+    stream = torch.cuda.current_stream()
+    pts_dev = torch.from_numpy(pts_np).cuda()
+    scene = nlos.scene_create(prm, pts_dev)
+    S, B, P = scene.num_scan, scene.num_bins, scene.num_points
+    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    counts = torch.empty((S, B), dtype=torch.int32, device="cuda")
+    energy = torch.empty(S, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    pairs_per_step = S * P
+
+    def step():
+        nlos.scene_set_points(scene, pts_dev)
+        nlos.forward(scene, tau)
+        nlos.detect(scene, tau, counts, energy)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    nlos.scene_check(scene)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # evict L2 between timed steps (outside the step events)
+        e = ev[k]
+        e[0].record(stream)
+        nlos.scene_set_points(scene, pts_dev)
+        e[1].record(stream)
+        nlos.forward(scene, tau)
+        e[2].record(stream)
+        nlos.detect(scene, tau, counts, energy)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    nlos.scene_check(scene)
+    step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
+    fwd_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
+    t_total = float(step_ms.sum()) * 1e-3
+    if dist:
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = ws * args.steps * pairs_per_step / t_total
+
+    # ---- end to end through the C ABI with host buffers (pinned) ----------
+    pts_host = torch.from_numpy(pts_np).pin_memory()
+    counts_host = torch.empty((S, B), dtype=torch.int32).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for _ in range(2):
+        nlos.scene_set_points(scene, pts_host)
+        nlos.forward(scene, tau)
+        nlos.detect(scene, tau, counts, energy)
+        counts_host.copy_(counts, non_blocking=True)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = e2e_ev[k]
+        a.record(stream)
+        nlos.scene_set_points(scene, pts_host)          # H2D of the step's points
+        nlos.forward(scene, tau)
+        nlos.detect(scene, tau, counts, energy)
+        counts_host.copy_(counts, non_blocking=True)    # D2H of the step's result
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_t = sum(a.elapsed_time(b) for a, b in e2e_ev) * 1e-3
+    if dist:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = {"value": ws * args.steps * pairs_per_step / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(pts_np.nbytes), "d2h_bytes_per_step": int(S * B * 4)}
+
+    # ---- roofline of the dominant kernel (the pair histogram) -------------
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_pairs = n_sm * 128 * sm_max * 1e6 / FP32_SLOTS_PER_PAIR
+    fwd_mean = float(fwd_ms.mean()) * 1e-3
+    achieved = pairs_per_step / fwd_mean
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9,
+            "unit": "Gpair/s", "frac": achieved / peak_pairs,
+            "traffic": _traffic_for(os.path.join(ROOT, "paper_2506_03747_gb300", "csrc",
+                                                 "forward.cu")),
+            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / "
+                          f"{FP32_SLOTS_PER_PAIR} FP32 slots per pair",
+            "kernel_ms": fwd_mean * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "scan_points": S, "bins": B, "points": P,
+                       "pairs_per_step": pairs_per_step,
+                       "l2": "flushed by a 256 MB write between timed steps (outside the step "
+                             "events)",
+                       "step": "scene_set_points (pack) + forward (pair histogram + fused "
+                               "jitter) + detect (FP64 energy/peak + Poisson noise)",
+                       "parallelism": f"{ws} independent scenes, one per GPU"},
+            "transients_per_s": ws * args.steps * S / t_total,
+            "wall_s": wall, "clocks": clk, "gpu_launches": 4 * args.steps,
+            "roofline": roof, "e2e": e2e}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(params, pts_np, args.cpu_scan)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    scene.destroy()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle CPU baseline (profiling runs)")
+    ap.add_argument("--cpu-scan", type=int, default=2048,
+                    help="scan points in the CPU baseline sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

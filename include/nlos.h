@@ -1,0 +1,280 @@
+/*
+ * nlos.h - C ABI of the GB300 (sm_103a) NLOS transient simulator.
+ *
+ * Implements the forward model of Shi et al., "Fast Non-Line-of-Sight
+ * Transient Data Simulation and an Open Benchmark Dataset" (arXiv 2506.03747):
+ * the confocal transient integral of the Theory section (Eq. 1; display
+ * equations are numbered here in order of appearance), evaluated directly as
+ * a sum over (scan point, surface point) pairs and generalised to non-confocal
+ * scans, stand-off legs, Lambertian cosines and patch areas; then the
+ * detector's Gaussian timing jitter (Eq. 16/17, Algorithm 1 step 2.3) and
+ * seeded Poisson photon + dark-count noise (Eq. 18/19, Algorithm 1 step 2.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an nlos_status; NLOS_OK is 0. On failure
+ *    nlos_last_error() returns a thread-local message (valid until the next
+ *    call on that thread). No exception, exit, abort or device trap ever
+ *    crosses this boundary.
+ *  - "Device pointer" arguments are CUDA global-memory pointers on the current
+ *    device; they are caller-owned unless stated otherwise and must be 16-byte
+ *    aligned. "cuda_stream" is a cudaStream_t (NULL = legacy default stream).
+ *    Work is enqueued asynchronously on that stream unless a call says it
+ *    waits.
+ *  - Geometry: the relay wall is the plane z = 0 with normal +z, centred at
+ *    the origin; hidden surface points have z > 0. The scan grid has
+ *    scan_nx x scan_ny cell-centred spots over [-w_x, w_x] x [-w_y, w_y];
+ *    scan point s = iy * scan_nx + ix. Transient cubes are float32
+ *    [scan_ny][scan_nx][num_bins] (time bin fastest), the paper's
+ *    N x N x M layout.
+ *  - Point record (float32, 8 per point, "AoS8"): x, y, z, nx, ny, nz,
+ *    albedo, area, in metres; (nx, ny, nz) is a unit normal pointing away
+ *    from the surface; albedo in [0, 1] (the paper's A/255), area > 0.
+ *  - c = 299 792 458 m/s.
+ */
+#ifndef NLOS_H
+#define NLOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NLOS_ABI_VERSION 1
+
+typedef enum {
+  NLOS_OK = 0,
+  NLOS_EINVAL = 1,      /* bad argument (message says which) */
+  NLOS_ENOMEM = 2,      /* device or host allocation failed, or budget refused */
+  NLOS_ECUDA = 3,       /* a CUDA runtime call failed */
+  NLOS_ETIMEOUT = 4,    /* a bounded device or host wait ran out */
+  NLOS_EBUSY = 5,       /* result not ready yet (serving) */
+  NLOS_ECANCELLED = 6,  /* request was cancelled (serving) */
+  NLOS_ENOTFOUND = 7    /* unknown ticket (serving) */
+} nlos_status;
+
+typedef enum { NLOS_CONFOCAL = 0, NLOS_NONCONFOCAL = 1 } nlos_scan_mode;
+
+/* Stand-off (the paper's "stand-off distance", abstract and Introduction):
+ * the laser/SPAD optics sit at D = (0, 0, standoff_m) in front of the wall
+ * centre. EUCLIDEAN adds the legs |D - l_s| + |d_s - D| to every path;
+ * CONSTANT adds 2 * standoff_m (0 gives Eq. 1 exactly, with no device legs). */
+typedef enum { NLOS_STANDOFF_EUCLIDEAN = 0, NLOS_STANDOFF_CONSTANT = 1 } nlos_standoff_mode;
+
+/* Cosine terms of the pair weight w = albedo * area * C / (|x-l|^2 |x-d|^2):
+ * NONE: C = 1 (Eq. 1 as printed: albedo / r^4 for a confocal scan);
+ * OBJECT (default): C = max(0, cos_l) * max(0, cos_d), the Lambertian object
+ *   cosines n.(l-x)/|l-x| and n.(d-x)/|d-x| (back-facing patches give no light);
+ * OBJECT_WALL: additionally the wall-side cosines (x-l)_z/|x-l| * (x-d)_z/|x-d|. */
+typedef enum { NLOS_COS_NONE = 0, NLOS_COS_OBJECT = 1, NLOS_COS_OBJECT_WALL = 2 } nlos_cos_mode;
+
+/* Noise (Eq. 18/19). PEAK: lambda = (peak_photons / max tau_G) * tau_G +
+ * dark_per_bin, counts ~ Poisson(lambda). PAPER_NR (Algorithm 1 step 2.4):
+ * sigma_n = Var(tau_G) / 10^(nr_db/10) over the whole cube, lambda =
+ * sigma_n * tau_G + dark_per_bin; the paper's noisy transient is counts / sigma_n
+ * (sigma_n is reported in nlos_stats.noise_scale). */
+typedef enum { NLOS_NOISE_NONE = 0, NLOS_NOISE_PEAK = 1, NLOS_NOISE_PAPER_NR = 2 } nlos_noise_mode;
+
+/* NEAREST: bin b = floor(u) of the path-bin coordinate u, then the Gaussian
+ * jitter convolution (Algorithm 1: blur, then noise). SPLAT: each pair spreads
+ * its weight as w * phi_sigma(b + 1/2 - u) over the bins with
+ * |b + 1/2 - u| < 6 sigma (differentiable; no separate blur). */
+typedef enum { NLOS_BIN_NEAREST = 0, NLOS_BIN_SPLAT = 1 } nlos_bin_mode;
+
+/* Scene and system parameters (the paper's parameter list: relay surface
+ * extent and sampling, stand-off, bin width, acquisition window, jitter FWHM,
+ * noise level; abstract, Introduction and Algorithm 1 inputs). */
+typedef struct {
+  uint32_t struct_size;       /* sizeof(nlos_params), for ABI versioning */
+  uint32_t scan_nx, scan_ny;  /* spatial sampling N (>= 1 each) */
+  double wall_half_x;         /* w: half side of the scanned area [m] (> 0) */
+  double wall_half_y;
+  int32_t scan_mode;          /* nlos_scan_mode */
+  double laser_x, laser_y;    /* fixed laser spot on the wall (non-confocal) [m] */
+  double standoff_m;          /* >= 0 */
+  int32_t standoff_mode;      /* nlos_standoff_mode */
+  double bin_width_s;         /* Delta t [s] (> 0) */
+  uint32_t num_bins;          /* M: bins in the acquisition window (1 .. 65536) */
+  double window_start_m;      /* path length at the start of bin 0 [m];
+                                 NaN = the device legs of the wall centre
+                                 (2 * standoff_m), i.e. t = 0 at the first
+                                 bounce on the wall centre, as in Eq. 1 */
+  double jitter_fwhm_s;       /* Gaussian jitter FWHM [s]; 0 = none */
+  int32_t bin_mode;           /* nlos_bin_mode */
+  int32_t cos_mode;           /* nlos_cos_mode */
+  int32_t noise_mode;         /* nlos_noise_mode */
+  float peak_photons;         /* PEAK mode: expected counts at the cube maximum */
+  float dark_per_bin;         /* dark counts added to lambda in every bin */
+  float nr_db;                /* PAPER_NR mode: the paper's noise level nr */
+  uint64_t seed;              /* Philox key (seed_lo, seed_hi) */
+  uint32_t stream_tag;        /* word 3 of every Philox counter */
+  float boundary_eps;         /* > 0: count pairs with u within eps of a bin
+                                 edge (nlos_stats.boundary_pairs); 0 = off */
+} nlos_params;
+
+/* Fills *p with the defaults: 32x32 confocal scan of a 1 m x 1 m wall, no
+ * stand-off, 256 bins of 16 ps, no jitter, COS_OBJECT, no noise. */
+void nlos_params_default(nlos_params* p);
+
+typedef struct {
+  uint32_t struct_size;       /* set by the caller to sizeof(nlos_stats) */
+  uint64_t pairs;             /* scan points x surface points evaluated */
+  double peak;                /* max over the cube of tau_G (float32 value) */
+  double noise_scale;         /* lambda = noise_scale * tau_G + noise_dark */
+  double noise_dark;
+  double mean;                /* mean of tau_G over the cube (FP64 sum / n) */
+  double variance;            /* population variance of tau_G (FP64) */
+  uint64_t boundary_pairs;    /* pairs with u within boundary_eps of a bin edge */
+  uint32_t device_error;      /* nonzero: a bounded device wait gave up */
+} nlos_stats;
+
+typedef struct nlos_scene nlos_scene;
+
+/* Creates a scene: validates the parameters and the points, copies the points
+ * to the device and precomputes per-point and per-scan-point terms (FP64 on
+ * the device, stored FP32). points_aos8 is host memory when
+ * points_on_device == 0, else a device pointer; it is not retained.
+ * Points must have finite coordinates, z > 0, area > 0 and albedo >= 0
+ * (NLOS_EINVAL otherwise). The call waits for the stream (it checks the
+ * points on the device). The library owns the scene's device memory until
+ * nlos_scene_destroy. num_points may be 0 (the transient is then zero). */
+nlos_status nlos_scene_create(const nlos_params* params, const float* points_aos8,
+                              uint64_t num_points, int points_on_device, void* cuda_stream,
+                              nlos_scene** out);
+
+/* Replaces the points of a scene by num_points new records (same count as at
+ * creation), re-running the ingest/pack step on cuda_stream. Asynchronous:
+ * invalid points are reported by the next nlos_simulate with stats
+ * (device_error bit 2) or by nlos_scene_check. points_aos8 is host memory
+ * (pinned memory keeps the copy asynchronous) when points_on_device == 0. */
+nlos_status nlos_scene_set_points(nlos_scene* scene, const float* points_aos8, uint64_t num_points,
+                                  int points_on_device, void* cuda_stream);
+
+/* Waits for cuda_stream and reports invalid points or a device wait that gave
+ * up since the scene was created (NLOS_EINVAL / NLOS_ETIMEOUT). */
+nlos_status nlos_scene_check(nlos_scene* scene, void* cuda_stream);
+
+/* Frees the scene (waits for work that uses it on its creation stream). */
+nlos_status nlos_scene_destroy(nlos_scene* scene);
+
+/* Number of scan points, bins and points of a scene. */
+nlos_status nlos_scene_shape(const nlos_scene* scene, uint64_t* num_scan, uint32_t* num_bins,
+                             uint64_t* num_points);
+
+/* The forward pass (the whole hot path) for a scene:
+ *   tau_dev    [S][B] float32 device, required: the noise-free transient,
+ *              after the jitter convolution (NEAREST) or the splat (SPLAT);
+ *   counts_dev [S][B] uint32 device, nullable: Poisson counts (noise_mode !=
+ *              NONE; with NONE it must be NULL);
+ *   energy_dev [S] double device, nullable: per-transient FP64 sum of tau_dev;
+ *   stats      host, nullable: when given, the call waits for the stream and
+ *              fills it.
+ * Asynchronous on cuda_stream otherwise. Calls on one scene must not overlap
+ * on the device (they share its scratch): use one stream per scene. */
+nlos_status nlos_simulate(nlos_scene* scene, float* tau_dev, uint32_t* counts_dev,
+                          double* energy_dev, nlos_stats* stats, void* cuda_stream);
+
+/* The two halves of nlos_simulate, for callers that time or overlap them:
+ * nlos_forward: the pair histogram with the fused jitter (NEAREST) or the
+ *   splat (SPLAT) into tau_dev [S][B] (overwritten);
+ * nlos_detect: on a forward result, the per-transient energy (energy_dev,
+ *   nullable), the cube maximum / sums and the Poisson counts (counts_dev,
+ *   nullable; noise_mode != NONE). Both asynchronous. */
+nlos_status nlos_forward(nlos_scene* scene, float* tau_dev, void* cuda_stream);
+nlos_status nlos_detect(nlos_scene* scene, const float* tau_dev, uint32_t* counts_dev,
+                        double* energy_dev, void* cuda_stream);
+
+/* Adjoint of the SPLAT forward (bin_mode must be SPLAT): given grad_tau_dev
+ * = dL/dtau ([S][B] float32 device), writes dL/d albedo_p and dL/d delta_p
+ * ([P] float32 device each, nullable), where delta_p displaces point p along
+ * its normal (normal and area held fixed), evaluated at delta = 0. */
+nlos_status nlos_simulate_backward(nlos_scene* scene, const float* grad_tau_dev,
+                                   float* grad_albedo_dev, float* grad_depth_dev,
+                                   void* cuda_stream);
+
+/* ---- Step-level entry points (each one step of the hot path) ------------ */
+
+/* Gaussian jitter (Eq. 16/17): out[t][b] = sum_j g_j in[t][b - j], j = -R..R,
+ * R = ceil(2 sigma), sigma = fwhm_s / (2 sqrt(2 ln 2) bin_width_s), taps
+ * exp(-j^2 / (2 sigma^2)) normalised to sum 1, zero padding; fwhm_s = 0 copies.
+ * in and out are [num_traces][num_bins] float32 device and must not overlap. */
+nlos_status nlos_jitter(const float* in_dev, float* out_dev, uint64_t num_traces,
+                        uint32_t num_bins, double fwhm_s, double bin_width_s, void* cuda_stream);
+
+/* Per-trace FP64 energy (energy_dev [num_traces], nullable) and the cube's
+ * maximum and FP64 sum / sum of squares (written to stats_dev, nullable:
+ * {double max, double sum, double sumsq}). Asynchronous. */
+nlos_status nlos_reduce(const float* tau_dev, uint64_t num_traces, uint32_t num_bins,
+                        double* energy_dev, double* stats_dev, void* cuda_stream);
+
+/* Poisson noise: counts[i] ~ Poisson(fmaf(scale, tau[i], dark)) drawn from
+ * the Philox4x32-10 stream of global bin index index_base + i: key =
+ * (seed_lo, seed_hi), counter = (index_lo, index_hi, block, stream_tag),
+ * uniforms ((word >> 9) + 0.5) * 2^-23; Knuth's multiplication method for
+ * lambda < 10, Hoermann's PTRS (1993) otherwise, in single precision. */
+nlos_status nlos_noise(const float* tau_dev, uint64_t n, float scale, float dark, uint64_t seed,
+                       uint32_t stream_tag, uint64_t index_base, uint32_t* counts_dev,
+                       void* cuda_stream);
+
+/* Raw Philox4x32-10 (Salmon et al., SC'11) words: out[i] (4 words) =
+ * philox(counter_i, key) for the n counters in ctr_dev ([n][4] uint32
+ * device), key = (key0, key1). */
+nlos_status nlos_philox(const uint32_t* ctr_dev, uint64_t n, uint32_t key0, uint32_t key1,
+                        uint32_t* out_dev, void* cuda_stream);
+
+/* Debug/parity: the forward kernel's own per-pair path-bin coordinate u and
+ * weight w (float32, [s_count][P] device each, nullable) for scan points
+ * s_begin .. s_begin + s_count - 1, computed by the same device code. */
+nlos_status nlos_pair_table(nlos_scene* scene, uint64_t s_begin, uint64_t s_count, float* u_dev,
+                            float* w_dev, void* cuda_stream);
+
+/* ---- Serving: continuous batching of simulation requests ---------------- */
+
+typedef struct nlos_server nlos_server;
+
+/* Creates a server that admits requests while the device memory they hold
+ * stays within hbm_budget_bytes, and runs their work from one persistent
+ * kernel launch per batch. */
+nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out);
+
+/* Queues a request (points are host memory, copied); returns its ticket. */
+nlos_status nlos_serve_submit(nlos_server* server, const nlos_params* params,
+                              const float* points_aos8, uint64_t num_points, uint64_t* ticket_out);
+
+/* Waits up to wait_ms (0 = poll) for a result. NLOS_EBUSY while pending;
+ * on NLOS_OK the device pointers (owned by the server, valid until
+ * nlos_serve_release) and stats are filled (each output nullable). */
+nlos_status nlos_serve_poll(nlos_server* server, uint64_t ticket, int wait_ms,
+                            const float** tau_dev_out, const uint32_t** counts_dev_out,
+                            nlos_stats* stats);
+
+/* Invalidates the ticket: cancels a pending request, frees a finished one, or
+ * (admitted request) frees its memory as soon as its device work completes. */
+nlos_status nlos_serve_release(nlos_server* server, uint64_t ticket);
+
+/* Waits (up to 30 s) for admitted requests, cancels pending ones, stops the
+ * scheduler and frees everything. */
+nlos_status nlos_server_destroy(nlos_server* server);
+
+/* Monitoring: device bytes held by admitted requests, and the numbers of
+ * pending and admitted requests (each output nullable). */
+nlos_status nlos_server_stats(nlos_server* server, uint64_t* resident_bytes, uint32_t* pending,
+                              uint32_t* active);
+
+/* Testing of failure handling, host side only: arms one fault for the next
+ * request the scheduler handles. 1 = withhold the publication of its first
+ * work item (the device's bounded wait gives up after about a second and the
+ * request fails with NLOS_ETIMEOUT, while the server keeps running);
+ * 2 = refuse its device allocation (the request fails with NLOS_ENOMEM). */
+nlos_status nlos_server_inject(nlos_server* server, int fault);
+
+/* ---- Misc ---------------------------------------------------------------- */
+
+const char* nlos_last_error(void);
+int nlos_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLOS_H */

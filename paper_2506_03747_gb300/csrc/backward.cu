@@ -1,0 +1,191 @@
+// Adjoint of the Gaussian-splat forward (differentiable form of the binned
+// transient of arXiv 2506.03747): gradients of a loss L(tau) with respect to
+// per-point albedo rho_p and per-point displacement delta_p along the normal.
+//
+// For a pair (s, p) with x_b = b + 1/2 - u_sp and phi the splat kernel,
+//   G0 = sum_b g[s][b] phi(x_b),   G1 = sum_b g[s][b] (x_b / sigma^2) phi(x_b),
+//   dL/d rho_p   = sum_s (dw/d rho) G0,
+//   dL/d delta_p = sum_s (dw/d delta) G0 + w (du/d delta) G1,
+// with, for x -> x + delta n: dr/d delta = -cos, d cos/d delta = -(1 - cos^2)/r,
+// d(z/r)/d delta = (n_z + (z/r) cos)/r and du/d delta = -(cos_l + cos_d)/(c dt).
+//
+// Schedule: one CTA per (32-scan-point tile, point block); the tile's g rows
+// are staged into shared memory as [bin][32] (lane = scan point, conflict-free
+// gathers); points are broadcast from shared memory; each lane gathers the taps
+// of its own scan point, a warp sum over the 32 scan points gives the tile's
+// contribution to each point, added to the outputs with one global atomic.
+#include "common.cuh"
+#include "device_util.cuh"
+
+#include <cmath>
+
+namespace nlos {
+
+namespace {
+
+constexpr int kBwdTile = 32;
+constexpr int kBwdPoints = 256;  // points per CTA
+
+struct BwdArgs {
+  const float* raw;        // [P][8]
+  const ScanPoint* scan;   // spots and offsets
+  const float* g;          // [S][B]
+  float* ga;               // [P] or null
+  float* gd;               // [P] or null
+  uint64_t P, S;
+  uint32_t B;
+  int scan_mode, cos_mode;
+  float lx, ly;            // laser spot (non-confocal)
+  float inv_cdt;           // 1 / (c dt)
+  float inv2s2, inv_s2, norm, reach, qstep;
+};
+
+// Leg factor F = cosf * wallf / r^2 and its delta-derivative (FP32).
+__device__ __forceinline__ void leg(int cos_mode, float ndotv, float vz, float nz, float r,
+                                    float& F, float& dF, float& c) {
+  const float ri = 1.0f / r;
+  c = -ndotv * ri;
+  const float dc = -(1.0f - c * c) * ri;
+  float fc = 1.0f, dfc = 0.0f;
+  if (cos_mode >= NLOS_COS_OBJECT) {
+    if (c > 0.0f) {
+      fc = c;
+      dfc = dc;
+    } else {
+      fc = 0.0f;
+      dfc = 0.0f;
+    }
+  }
+  float fw = 1.0f, dfw = 0.0f;
+  if (cos_mode == NLOS_COS_OBJECT_WALL) {
+    fw = vz * ri;
+    dfw = (nz + fw * c) * ri;
+  }
+  const float ri2 = ri * ri;
+  F = fc * fw * ri2;
+  // d(r^-2)/d delta = -2 r^-3 dr/d delta = 2 c r^-3
+  dF = (dfc * fw + fc * dfw) * ri2 + fc * fw * 2.0f * c * ri2 * ri;
+}
+
+__global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs a) {
+  extern __shared__ float sm[];
+  float* gt = sm;                                   // [B][32]
+  float* pts = sm + (size_t)a.B * kBwdTile;         // [kBwdPoints][8]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const uint64_t n_pblk = (a.P + kBwdPoints - 1) / kBwdPoints;
+  const uint64_t tile = blockIdx.x / n_pblk;
+  const uint64_t p0 = (blockIdx.x % n_pblk) * kBwdPoints;
+  const int np = (int)min((uint64_t)kBwdPoints, a.P - p0);
+
+  for (uint32_t i = tid; i < a.B * kBwdTile; i += blockDim.x) {
+    const uint32_t s_loc = i & 31, b = i >> 5;
+    const uint64_t s = tile * kBwdTile + s_loc;
+    gt[i] = s < a.S ? a.g[s * a.B + b] : 0.0f;
+  }
+  for (int i = tid; i < np * 8; i += blockDim.x) pts[i] = a.raw[p0 * 8 + i];
+  __syncthreads();
+
+  const uint64_t s = tile * kBwdTile + lane;
+  const bool valid = s < a.S;
+  ScanPoint sp = valid ? a.scan[s] : ScanPoint{0.f, 0.f, -1e30f, 0.f};
+  const float dx_s = sp.sx, dy_s = sp.sy;
+  const float lx = a.scan_mode == NLOS_CONFOCAL ? sp.sx : a.lx;
+  const float ly = a.scan_mode == NLOS_CONFOCAL ? sp.sy : a.ly;
+
+  for (int i = warp; i < np; i += nwarps) {
+    const float* q = pts + 8 * i;
+    const float x = q[0], y = q[1], z = q[2], nx = q[3], ny = q[4], nz = q[5], rho = q[6],
+                area = q[7];
+    // laser leg l -> x and detector leg d -> x
+    const float vlx = x - lx, vly = y - ly, vlz = z;
+    const float vdx = x - dx_s, vdy = y - dy_s, vdz = z;
+    const float rl = sqrtf(vlx * vlx + vly * vly + vlz * vlz);
+    const float rd = sqrtf(vdx * vdx + vdy * vdy + vdz * vdz);
+    float Fl, dFl, cl, Fd, dFd, cd;
+    leg(a.cos_mode, nx * vlx + ny * vly + nz * vlz, vlz, nz, rl, Fl, dFl, cl);
+    leg(a.cos_mode, nx * vdx + ny * vdy + nz * vdz, vdz, nz, rd, Fd, dFd, cd);
+    const float qw = rho * area;
+    const float w = qw * Fl * Fd;
+    const float dw_drho = area * Fl * Fd;
+    const float dw_dd = qw * (dFl * Fd + Fl * dFd);
+    // u relative to bin 0: legs and window start are in sp.off (both legs
+    // below are recomputed here rather than taken from the packed form)
+    const float u = (rl + rd) * a.inv_cdt + sp.off;
+    const float du_dd = -(cl + cd) * a.inv_cdt;
+    float G0 = 0.f, G1 = 0.f;
+    if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f)) {
+      const int lo = max(0, (int)(floorf(u - 0.5f - a.reach) + 1.0f));
+      const int hi = min((int)a.B - 1, (int)(ceilf(u - 0.5f + a.reach) - 1.0f));
+      if (lo <= hi) {
+        float xb = (float)lo + 0.5f - u;
+        float K = a.norm * expf(-xb * xb * a.inv2s2);
+        float r = expf(-(2.0f * xb + 1.0f) * a.inv2s2);
+        for (int b = lo; b <= hi; ++b) {
+          const float gv = gt[b * kBwdTile + lane];
+          G0 = fmaf(gv, K, G0);
+          G1 = fmaf(gv * xb, K, G1);
+          K *= r;
+          r *= a.qstep;
+          xb += 1.0f;
+        }
+        G1 *= a.inv_s2;
+      }
+    }
+    float ca = dw_drho * G0;
+    float cdl = dw_dd * G0 + w * du_dd * G1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ca += __shfl_xor_sync(0xffffffffu, ca, o);
+      cdl += __shfl_xor_sync(0xffffffffu, cdl, o);
+    }
+    if (lane == 0) {
+      if (a.ga) atomicAdd(a.ga + p0 + i, ca);
+      if (a.gd) atomicAdd(a.gd + p0 + i, cdl);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* grad_albedo,
+                            float* grad_depth, cudaStream_t st) {
+  const Geometry& g = sc.g;
+  cudaError_t e;
+  if (grad_albedo && (e = cudaMemsetAsync(grad_albedo, 0, sizeof(float) * g.P, st)) != cudaSuccess)
+    return e;
+  if (grad_depth && (e = cudaMemsetAsync(grad_depth, 0, sizeof(float) * g.P, st)) != cudaSuccess)
+    return e;
+  if (g.P == 0 || g.S == 0) return cudaSuccess;
+  BwdArgs a{};
+  a.raw = sc.raw_points;
+  a.scan = sc.scan;
+  a.g = grad_tau;
+  a.ga = grad_albedo;
+  a.gd = grad_depth;
+  a.P = g.P;
+  a.S = g.S;
+  a.B = g.B;
+  a.scan_mode = g.scan_mode;
+  a.cos_mode = g.cos_mode;
+  a.lx = (float)sc.params.laser_x;
+  a.ly = (float)sc.params.laser_y;
+  a.inv_cdt = (float)(1.0 / g.cdt);
+  const double s = g.sigma;
+  a.inv2s2 = (float)(1.0 / (2.0 * s * s));
+  a.inv_s2 = (float)(1.0 / (s * s));
+  a.norm = (float)(1.0 / (s * std::sqrt(2.0 * 3.14159265358979323846)));
+  a.reach = (float)(6.0 * s);
+  a.qstep = (float)std::exp(-1.0 / (s * s));
+  const size_t smem = sizeof(float) * ((size_t)g.B * kBwdTile + kBwdPoints * 8);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sc.device);
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t blocks = ((g.P + kBwdPoints - 1) / kBwdPoints) * ((g.S + kBwdTile - 1) / kBwdTile);
+  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+  bwd_kernel<<<(unsigned)blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace nlos

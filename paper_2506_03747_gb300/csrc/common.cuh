@@ -1,0 +1,128 @@
+// Internal declarations of the GB300 NLOS simulator library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nlos.h"
+
+namespace nlos {
+
+constexpr double kLightSpeed = 299792458.0;
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message behind nlos_last_error()).
+// ---------------------------------------------------------------------------
+nlos_status set_error(nlos_status st, const std::string& msg);
+nlos_status cuda_error(cudaError_t e, const char* what);
+void clear_error();
+
+#define NLOS_CUDA_TRY(expr)                                     \
+  do {                                                          \
+    cudaError_t _e = (expr);                                    \
+    if (_e != cudaSuccess) return ::nlos::cuda_error(_e, #expr); \
+  } while (0)
+
+// Device-side status word bits (scene scratch).
+constexpr uint32_t kErrWaitTimeout = 1u;   // a bounded mbarrier wait gave up
+constexpr uint32_t kErrBadPoint = 2u;      // point validation failed
+
+// ---------------------------------------------------------------------------
+// Packed surface points, two per record, interleaved component-wise
+// (.x = point 2k, .y = point 2k + 1), 64 bytes:
+//   px, py      position x, y
+//   pz2         z^2
+//   kq          weight factor (cosine-free modes)
+//   na, nb, nc  cosine numerator na*(px - sx) + nb*(py - sy) + nc at scan spot
+//               (sx, sy, 0), i.e. n.(spot - x) = -(nx dx + ny dy + nz z) times a
+//               per-point factor folded in at packing
+//   uoff        the point's own path-bin offset (laser leg of a non-confocal
+//               scan, in bins; 0 for a confocal scan)
+// An odd point count is padded with a point that never reaches a bin.
+// ---------------------------------------------------------------------------
+struct __align__(16) PointPair {
+  float2 px, py, pz2, kq, na, nb, nc, uoff;
+};
+static_assert(sizeof(PointPair) == 64, "PointPair must be 64 bytes");
+
+// Per-scan-point record: spot (sx, sy), bin offset off_s = (legs(s) - L0)/(c dt).
+struct __align__(16) ScanPoint {
+  float sx, sy, off, pad;
+};
+
+// Device scratch owned by a scene (one per scene). The error word is sticky
+// (cleared by nlos_scene_check); the rest is reset by every forward pass.
+struct SceneScratch {
+  unsigned int err;           // kErr* bits
+  unsigned int pad;
+  // --- reset per pass from here ---
+  unsigned int peak_bits;     // max of tau_G as float bits (values are >= 0)
+  unsigned int pad2;
+  unsigned long long boundary_pairs;
+  double sum;                 // FP64 sum of tau_G over the cube
+  double sumsq;               // FP64 sum of squares
+  float scale;                // noise scale (computed on the device)
+  float dark;
+};
+constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
+static_assert(sizeof(SceneScratch) == 48, "scratch layout");
+
+struct Geometry {
+  // host-side resolved parameters
+  uint32_t nx, ny, B;
+  uint64_t S, P;
+  int scan_mode, cos_mode, bin_mode, noise_mode;
+  double cdt;        // c * dt [m]
+  double L0;         // window start [m]
+  double sigma;      // jitter sigma in bins (0: none)
+};
+
+struct SceneImpl;
+
+// Forward kernel launch (forward.cu). tau must be zeroed beforehand; the
+// kernel adds its (jittered, for NEAREST) partial histograms into it.
+cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st);
+cudaError_t launch_pair_table(const SceneImpl& sc, uint64_t s_begin, uint64_t s_count, float* u,
+                              float* w, cudaStream_t st);
+// Adjoint (backward.cu).
+cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* grad_albedo,
+                            float* grad_depth, cudaStream_t st);
+
+// Detector kernels (detector.cu).
+int jitter_taps(double sigma, float* taps, int max_taps);  // returns k
+cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t B, double sigma,
+                          cudaStream_t st);
+cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double* energy,
+                          SceneScratch* scratch, cudaStream_t st);
+cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,
+                         uint32_t stream_tag, uint64_t index_base, uint32_t* counts,
+                         cudaStream_t st);
+// Noise for a scene: scale from the scene's reduction results (scratch).
+cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scratch, int mode,
+                               float peak_photons, float dark, float nr_db, uint64_t seed,
+                               uint32_t stream_tag, uint32_t* counts, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, uint64_t n, uint32_t k0, uint32_t k1,
+                          uint32_t* out, cudaStream_t st);
+
+// Scene internals shared by the host code of the library.
+struct SceneImpl {
+  nlos_params params;
+  Geometry g;
+  PointPair* pairs = nullptr;      // [ceil(P/2)]
+  ScanPoint* scan = nullptr;       // [S padded to the scan tile]
+  SceneScratch* scratch = nullptr; // device
+  float* raw_points = nullptr;     // [P][8] original records (for the adjoint)
+  cudaStream_t stream = nullptr;   // creation stream
+  int device = 0;
+  int num_sms = 0;
+};
+
+int jitter_radius(double sigma);
+
+}  // namespace nlos
+
+struct nlos_scene {
+  nlos::SceneImpl impl;
+};

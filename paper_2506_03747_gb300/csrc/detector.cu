@@ -1,0 +1,253 @@
+// Detector model kernels of the GB300 NLOS simulator (arXiv 2506.03747):
+//  * Gaussian timing jitter per transient (Eq. 16/17, Algorithm 1 step 2.3);
+//  * per-transient FP64 energy, and the cube's maximum / FP64 sum and sum of
+//    squares that set the noise scale;
+//  * seeded Poisson photon + dark-count noise (Eq. 18/19, Algorithm 1 step 2.4)
+//    from per-bin Philox4x32-10 counter streams.
+// All three are HBM-streaming kernels: coalesced row-wise reads and writes,
+// grids sized to the SM count.
+#include "common.cuh"
+#include "device_util.cuh"
+#include "noise_core.cuh"
+
+#include <cmath>
+
+namespace nlos {
+
+// ---------------------------------------------------------------------------
+// Jitter taps: sigma in bins, R = ceil(2 sigma), k = 2R + 1 (Eq. 17), sampled
+// Gaussian exp(-j^2 / (2 sigma^2)) normalised to sum 1 (computed in FP64 on
+// the host, stored FP32). sigma = 0 gives the identity (k = 1).
+// ---------------------------------------------------------------------------
+int jitter_taps(double sigma, float* taps, int max_taps) {
+  const int R = jitter_radius(sigma);
+  const int k = 2 * R + 1;
+  if (k > max_taps) return -k;
+  if (R == 0) {
+    taps[0] = 1.0f;
+    return 1;
+  }
+  static thread_local double t[4097];
+  double sum = 0.0;
+  for (int j = -R; j <= R; ++j) {
+    t[j + R] = std::exp(-(double)j * (double)j / (2.0 * sigma * sigma));
+    sum += t[j + R];
+  }
+  for (int j = 0; j < k; ++j) taps[j] = (float)(t[j] / sum);
+  return k;
+}
+
+constexpr int kJitterMaxTaps = 2049;  // R <= 1024 bins
+constexpr int kJitterTile = 1024;
+
+struct JitterArgs {
+  const float* in;
+  float* out;
+  uint64_t traces;
+  uint32_t B;
+  int R;
+  float taps[kJitterMaxTaps];
+};
+
+// One CTA = one run of kJitterTile output bins of one trace; the input run
+// with its R-bin halo is staged in shared memory (zero outside the trace).
+__global__ void jitter_kernel(const __grid_constant__ JitterArgs a) {
+  extern __shared__ float sm[];  // [kJitterTile + 2R] input
+  const uint32_t tiles_per_trace = (a.B + kJitterTile - 1) / kJitterTile;
+  const uint64_t t = blockIdx.x / tiles_per_trace;
+  const int b0 = (int)(blockIdx.x % tiles_per_trace) * kJitterTile;
+  const float* row = a.in + t * a.B;
+  for (int i = threadIdx.x; i < kJitterTile + 2 * a.R; i += blockDim.x) {
+    const int b = b0 - a.R + i;
+    sm[i] = (b >= 0 && b < (int)a.B) ? row[b] : 0.0f;
+  }
+  __syncthreads();
+  float* orow = a.out + t * a.B;
+  for (int i = threadIdx.x; i < kJitterTile; i += blockDim.x) {
+    const int b = b0 + i;
+    if (b >= (int)a.B) break;
+    float acc = 0.0f;
+    // out[b] = sum_j taps[j + R] * in[b - j]; in[b - j] sits at sm[i + R - j]
+    for (int j = -a.R; j <= a.R; ++j) acc = fmaf(a.taps[j + a.R], sm[i + a.R - j], acc);
+    orow[b] = acc;
+  }
+}
+
+cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t B, double sigma,
+                          cudaStream_t st) {
+  if (traces == 0 || B == 0) return cudaSuccess;
+  JitterArgs a;
+  a.in = in;
+  a.out = out;
+  a.traces = traces;
+  a.B = B;
+  const int k = jitter_taps(sigma, a.taps, kJitterMaxTaps);
+  if (k < 0) return cudaErrorInvalidValue;
+  a.R = (k - 1) / 2;
+  const uint64_t blocks = traces * ((B + kJitterTile - 1) / kJitterTile);
+  const size_t smem = sizeof(float) * (kJitterTile + 2 * a.R);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(jitter_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  jitter_kernel<<<(unsigned)blocks, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: one warp per transient. energy[t] = sum_b tau[t][b] in FP64;
+// cube maximum via atomicMax on the float bits (tau >= 0 orders like its
+// bits); FP64 sum and sum of squares via one double atomicAdd per warp.
+// ---------------------------------------------------------------------------
+__global__ void reduce_kernel(const float* __restrict__ tau, uint64_t traces, uint32_t B,
+                              double* energy, SceneScratch* scratch) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  double csum = 0.0, csq = 0.0;
+  float cmax = 0.0f;
+  for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < traces;
+       t += warps) {
+    const float* row = tau + t * B;
+    double s = 0.0, q = 0.0;
+    float m = 0.0f;
+    if ((B & 3u) == 0u) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+      for (uint32_t i = lane; i < B / 4; i += 32) {
+        const float4 v = __ldg(r4 + i);
+        s += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
+        q += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+      }
+    } else {
+      for (uint32_t i = lane; i < B; i += 32) {
+        const float v = __ldg(row + i);
+        s += (double)v;
+        q += (double)v * v;
+        m = fmaxf(m, v);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0 && energy) energy[t] = s;
+    csum += s;
+    csq += q;
+    cmax = fmaxf(cmax, m);
+  }
+  if (lane == 0 && scratch) {
+    atomicMax(&scratch->peak_bits, __float_as_uint(cmax));
+    atomicAdd(&scratch->sum, csum);
+    atomicAdd(&scratch->sumsq, csq);
+  }
+}
+
+cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double* energy,
+                          SceneScratch* scratch, cudaStream_t st) {
+  if (traces == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (traces + 7) / 8;
+  const unsigned blocks = (unsigned)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
+  reduce_kernel<<<blocks, 256, 0, st>>>(tau, traces, B, energy, scratch);
+  return cudaGetLastError();
+}
+
+struct NoiseArgs {
+  const float* tau;
+  uint32_t* counts;
+  uint64_t n;
+  uint64_t index_base;
+  uint64_t seed;
+  uint32_t tag;
+  float scale, dark;          // used when scratch == nullptr
+  SceneScratch* scratch;      // else: scale from the reduced cube
+  int mode;                   // nlos_noise_mode (scratch path)
+  float peak_photons, dark_cfg, nr_db;
+};
+
+__global__ void noise_kernel(const NoiseArgs a) {
+  float scale = a.scale, dark = a.dark;
+  if (a.scratch) {
+    scale = noise_scale_from(a.scratch, a.mode, a.peak_photons, a.nr_db, a.n);
+    dark = a.dark_cfg;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.scratch->scale = scale;
+      a.scratch->dark = dark;
+    }
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const float lam = fmaf(scale, __ldg(a.tau + i), dark);
+    a.counts[i] = poisson_sample(lam, a.index_base + i, a.seed, a.tag);
+  }
+}
+
+cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t want = (a.n + 255) / 256;
+  const unsigned blocks = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
+  noise_kernel<<<blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,
+                         uint32_t tag, uint64_t index_base, uint32_t* counts, cudaStream_t st) {
+  NoiseArgs a{};
+  a.tau = tau;
+  a.counts = counts;
+  a.n = n;
+  a.index_base = index_base;
+  a.seed = seed;
+  a.tag = tag;
+  a.scale = scale;
+  a.dark = dark;
+  a.scratch = nullptr;
+  return launch_noise_impl(a, st);
+}
+
+cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scratch, int mode,
+                               float peak_photons, float dark, float nr_db, uint64_t seed,
+                               uint32_t tag, uint32_t* counts, cudaStream_t st) {
+  NoiseArgs a{};
+  a.tau = tau;
+  a.counts = counts;
+  a.n = n;
+  a.index_base = 0;
+  a.seed = seed;
+  a.tag = tag;
+  a.scratch = scratch;
+  a.mode = mode;
+  a.peak_photons = peak_photons;
+  a.dark_cfg = dark;
+  a.nr_db = nr_db;
+  return launch_noise_impl(a, st);
+}
+
+// ---------------------------------------------------------------------------
+// Raw Philox words (parity testing of the device generator).
+// ---------------------------------------------------------------------------
+__global__ void philox_kernel(const uint4* ctr, uint64_t n, uint32_t k0, uint32_t k1, uint4* out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint64_t n, uint32_t k0, uint32_t k1,
+                          uint32_t* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(want < 4096 ? want : 4096);
+  philox_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const uint4*>(ctr), n, k0, k1,
+                                        reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace nlos

@@ -1,0 +1,202 @@
+// Forward transient kernel: the (scan point, surface point) pair sum of the
+// generalised Eq. 1 of Shi et al. (arXiv 2506.03747), accumulated as a
+// per-scan-point histogram over time bins, with the Gaussian jitter of
+// Eq. 16/17 fused into the write-out, or as the differentiable Gaussian splat.
+//
+// Layout and schedule (GB300, sm_103a):
+//  * One CTA tile = 32 scan points; lane l of every warp owns scan point l of
+//    the tile, so the shared histogram [bin][32] gives every lane its own bank
+//    and the shared atomics of a warp never conflict.
+//  * Surface points are packed in pairs (64 B, see PointPair) and staged into
+//    shared memory by 1-D TMA bulk copies, double-buffered on mbarriers. All
+//    warps of the CTA read the same staged block (broadcast loads) and split
+//    its pairs; each lane evaluates the two points of a pair for its scan
+//    point with packed FP32x2 arithmetic (__ffma2_rn & co.).
+//  * Work units (scan tile, bin window, point block) are split evenly over a
+//    persistent grid (stream-K): a CTA flushes its partial histogram into the
+//    zeroed output with vectorised global reductions whenever its (tile,
+//    window) changes. The jitter convolution is linear, so it is applied to
+//    each partial histogram during the flush.
+#include "forward_core.cuh"
+
+#include <algorithm>
+
+namespace nlos {
+
+// Standalone launch: the units of one job split evenly over a persistent grid.
+template <int SCAN, int COS, int MODE>
+__global__ void __launch_bounds__(1024, 1) fwd_kernel(const __grid_constant__ FwdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  FwdSmem sm;
+  sm.hist = reinterpret_cast<float*>(smem);
+  sm.stage = reinterpret_cast<PointPair*>(smem + (size_t)a.bw * kTile * 4);
+  sm.bars = reinterpret_cast<uint64_t*>(sm.stage + 2 * a.ppb);
+  const unsigned long long u0 = (unsigned long long)blockIdx.x * a.units / gridDim.x;
+  const unsigned long long u1 = (unsigned long long)(blockIdx.x + 1) * a.units / gridDim.x;
+  if (u0 >= u1) return;
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.bars[0], 1);
+    mbar_init(&sm.bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t it = 0;
+  unsigned long long nboundary = 0;
+  fwd_run<SCAN, COS, MODE>(a, u0, u1, sm, it, nboundary);
+  if (MODE == MODE_NEAREST_COUNT && nboundary) atomicAdd(a.boundary, nboundary);
+}
+
+// Per-pair table (debug/parity): the same pair_eval2 on pair k for scan point
+// s_begin + i; u relative to bin 0, w as accumulated.
+template <int SCAN, int COS>
+__global__ void pair_table_kernel(const PointPair* pairs, uint32_t n_pairs, uint32_t P,
+                                  const ScanPoint* scan, uint64_t s_begin, uint64_t s_count,
+                                  float kbin, float* u_out, float* w_out) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= s_count * n_pairs) return;
+  const uint64_t i = idx / n_pairs;
+  const uint32_t k = (uint32_t)(idx % n_pairs);
+  const ScanPoint sp = scan[s_begin + i];
+  PointPair q;
+  load_pair(pairs + k, q);
+  float2 u, w, cn;
+  pair_eval2<SCAN, COS>(q, make_float2(-sp.sx, -sp.sx), make_float2(-sp.sy, -sp.sy),
+                        make_float2(sp.sx, sp.sx), make_float2(sp.sy, sp.sy),
+                        make_float2(sp.off, sp.off), make_float2(kbin, kbin), u, w, cn);
+  if (!facing<COS>(cn.x)) w.x = 0.f;
+  if (!facing<COS>(cn.y)) w.y = 0.f;
+  const uint64_t p0 = 2ull * k;
+  if (u_out) {
+    u_out[i * P + p0] = u.x;
+    if (p0 + 1 < P) u_out[i * P + p0 + 1] = u.y;
+  }
+  if (w_out) {
+    w_out[i * P + p0] = w.x;
+    if (p0 + 1 < P) w_out[i * P + p0 + 1] = w.y;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+namespace {
+
+using FwdFn = void (*)(FwdArgs);
+
+template <int SCAN, int COS>
+FwdFn pick_mode(int mode) {
+  switch (mode) {
+    case MODE_NEAREST: return fwd_kernel<SCAN, COS, MODE_NEAREST>;
+    case MODE_NEAREST_COUNT: return fwd_kernel<SCAN, COS, MODE_NEAREST_COUNT>;
+    default: return fwd_kernel<SCAN, COS, MODE_SPLAT>;
+  }
+}
+
+FwdFn pick(int scan, int cos, int mode) {
+  if (scan == NLOS_CONFOCAL) {
+    if (cos == NLOS_COS_NONE) return pick_mode<NLOS_CONFOCAL, NLOS_COS_NONE>(mode);
+    if (cos == NLOS_COS_OBJECT) return pick_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT>(mode);
+    return pick_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(mode);
+  }
+  if (cos == NLOS_COS_NONE) return pick_mode<NLOS_NONCONFOCAL, NLOS_COS_NONE>(mode);
+  if (cos == NLOS_COS_OBJECT) return pick_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(mode);
+  return pick_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(mode);
+}
+
+}  // namespace
+
+int jitter_radius(double sigma) {
+  if (!(sigma > 0.0)) return 0;
+  return (int)std::ceil(2.0 * sigma);
+}
+
+cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
+  const Geometry& g = sc.g;
+  cudaError_t e = cudaMemsetAsync(tau, 0, sizeof(float) * g.S * g.B, st);
+  if (e != cudaSuccess || g.P == 0 || g.S == 0) return e;
+
+  FwdArgs a{};
+  a.pairs = sc.pairs;
+  a.scan = sc.scan;
+  a.tau = tau;
+  a.err = &sc.scratch->err;
+  a.boundary = &sc.scratch->boundary_pairs;
+  a.n_pairs = (uint32_t)((g.P + 1) / 2);
+  a.S = (uint32_t)g.S;
+  a.B = g.B;
+  a.kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
+  const bool splat = g.bin_mode == NLOS_BIN_SPLAT;
+  const int mode = splat ? MODE_SPLAT
+                         : (sc.params.boundary_eps > 0.f ? MODE_NEAREST_COUNT : MODE_NEAREST);
+  a.eps = sc.params.boundary_eps;
+  if (splat) {
+    const double s = g.sigma;
+    a.inv2s2 = (float)(1.0 / (2.0 * s * s));
+    a.norm = (float)(1.0 / (s * std::sqrt(2.0 * 3.14159265358979323846)));
+    a.reach = (float)(6.0 * s);
+    a.qstep = (float)std::exp(-1.0 / (s * s));
+    a.R = 0;
+    a.taps[0] = 1.0f;  // the flush writes the histogram unchanged
+  } else {
+    a.R = jitter_taps(g.sigma, a.taps, kMaxTaps);
+    a.R = (a.R - 1) / 2;
+  }
+
+  // shared memory: histogram [bw][32] floats + two staged blocks + barriers
+  int dev = sc.device, optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  a.ppb = kPairsPerBlock;
+  const size_t stage_bytes = 2 * (size_t)a.ppb * sizeof(PointPair) + 64;
+  uint32_t max_bw = (uint32_t)(((size_t)optin - stage_bytes) / (kTile * 4)) & ~3u;
+  a.n_win = (g.B + max_bw - 1) / max_bw;
+  a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
+  const size_t smem = (size_t)a.bw * kTile * 4 + stage_bytes;
+  const uint32_t n_tiles = (uint32_t)((g.S + kTile - 1) / kTile);
+  a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
+  a.units = (unsigned long long)n_tiles * a.n_win * a.n_blk;
+
+  FwdFn fn = pick(g.scan_mode, g.cos_mode, mode);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // 1024 threads when only one CTA fits on an SM, else 512 (register budget)
+  int threads = 512, per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm <= 1) {
+    threads = 1024;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  unsigned long long grid = (unsigned long long)sc.num_sms * per_sm;
+  if (grid > a.units) grid = a.units;
+  fn<<<(unsigned)grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_table(const SceneImpl& sc, uint64_t s_begin, uint64_t s_count, float* u,
+                              float* w, cudaStream_t st) {
+  const Geometry& g = sc.g;
+  const uint32_t n_pairs = (uint32_t)((g.P + 1) / 2);
+  const uint64_t total = s_count * n_pairs;
+  if (total == 0) return cudaSuccess;
+  const float kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  const PointPair* pp = sc.pairs;
+#define NLOS_PT(SC, CO)                                                                    \
+  pair_table_kernel<SC, CO><<<blocks, 256, 0, st>>>(pp, n_pairs, (uint32_t)g.P, sc.scan, \
+                                                    s_begin, s_count, kbin, u, w)
+  if (g.scan_mode == NLOS_CONFOCAL) {
+    if (g.cos_mode == NLOS_COS_NONE) NLOS_PT(NLOS_CONFOCAL, NLOS_COS_NONE);
+    else if (g.cos_mode == NLOS_COS_OBJECT) NLOS_PT(NLOS_CONFOCAL, NLOS_COS_OBJECT);
+    else NLOS_PT(NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL);
+  } else {
+    if (g.cos_mode == NLOS_COS_NONE) NLOS_PT(NLOS_NONCONFOCAL, NLOS_COS_NONE);
+    else if (g.cos_mode == NLOS_COS_OBJECT) NLOS_PT(NLOS_NONCONFOCAL, NLOS_COS_OBJECT);
+    else NLOS_PT(NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL);
+  }
+#undef NLOS_PT
+  return cudaGetLastError();
+}
+
+}  // namespace nlos

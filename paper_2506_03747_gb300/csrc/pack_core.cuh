@@ -1,0 +1,76 @@
+// Ingest/pack step of the GB300 NLOS simulator: per-point precomputation of
+// the packed pair records (FP64 arithmetic, FP32 storage) with validation.
+// Shared by scene creation and the persistent serving kernel.
+#pragma once
+
+#include "common.cuh"
+
+namespace nlos {
+
+// Packs point pairs (FP64 arithmetic on the device, FP32 storage) and checks
+// every point: finite values, z > 0, area > 0, albedo >= 0, |n| = 1 within 1e-3.
+//   confocal:     OBJECT: (na, nb, nc) = -sqrt(q) * (nx, ny, nz z);
+//                 WALL:   the same scaled by z; NONE: kq = q;
+//   non-confocal: K = q * max(0, cos_l) / r_l^2 (laser leg l -> x),
+//                 OBJECT: (na, nb, nc) = -K * (nx, ny, nz z); WALL: K * z / r_l * z;
+//                 NONE: kq = q / r_l^2; uoff = r_l / (c dt).
+// q = albedo * area.
+__device__ __forceinline__ void pack_pair(const float* __restrict__ raw, uint64_t P, uint64_t k,
+                                          int scan_mode, int cos_mode, double lx, double ly,
+                                          double inv_cdt, PointPair* pairs, unsigned int* err) {
+  float f[2][8];
+  for (int h = 0; h < 2; ++h) {
+    const uint64_t i = 2 * k + h;
+    if (i < P) {
+      const float* r = raw + 8 * i;
+      double nn = 0.0;
+      bool ok = true;
+      for (int c = 0; c < 8; ++c) ok = ok && isfinite(r[c]);
+      nn = (double)r[3] * r[3] + (double)r[4] * r[4] + (double)r[5] * r[5];
+      ok = ok && r[2] > 0.f && r[7] > 0.f && r[6] >= 0.f && fabs(nn - 1.0) <= 1e-3;
+      if (!ok) {
+        atomicOr(err, kErrBadPoint);
+      }
+      const double x = r[0], y = r[1], z = r[2], nx = r[3], ny = r[4], nz = r[5];
+      const double q = (double)r[6] * (double)r[7];
+      double kq = 0.0, s = 0.0, uoff = 0.0;
+      if (scan_mode == NLOS_CONFOCAL) {
+        if (cos_mode == NLOS_COS_NONE) kq = q;
+        else if (cos_mode == NLOS_COS_OBJECT) s = sqrt(q);
+        else s = sqrt(q) * z;
+      } else {
+        const double vx = x - lx, vy = y - ly, vz = z;
+        const double rl = sqrt(vx * vx + vy * vy + vz * vz);
+        const double cl = -(nx * vx + ny * vy + nz * vz) / rl;
+        uoff = rl * inv_cdt;
+        if (cos_mode == NLOS_COS_NONE) kq = q / (rl * rl);
+        else if (cos_mode == NLOS_COS_OBJECT) s = q * (cl > 0 ? cl : 0.0) / (rl * rl);
+        else s = q * (cl > 0 ? cl : 0.0) / (rl * rl) * (z / rl) * z;
+      }
+      f[h][0] = (float)x;
+      f[h][1] = (float)y;
+      f[h][2] = (float)(z * z);
+      f[h][3] = (float)kq;
+      f[h][4] = (float)(-s * nx);
+      f[h][5] = (float)(-s * ny);
+      f[h][6] = (float)(-s * nz * z);
+      f[h][7] = (float)uoff;
+    } else {
+      // padding: far away, no weight, no cosine -> never binned
+      f[h][0] = 0.f; f[h][1] = 0.f; f[h][2] = 1e30f; f[h][3] = 0.f;
+      f[h][4] = 0.f; f[h][5] = 0.f; f[h][6] = 0.f; f[h][7] = 1e30f;
+    }
+  }
+  PointPair o;
+  o.px = make_float2(f[0][0], f[1][0]);
+  o.py = make_float2(f[0][1], f[1][1]);
+  o.pz2 = make_float2(f[0][2], f[1][2]);
+  o.kq = make_float2(f[0][3], f[1][3]);
+  o.na = make_float2(f[0][4], f[1][4]);
+  o.nb = make_float2(f[0][5], f[1][5]);
+  o.nc = make_float2(f[0][6], f[1][6]);
+  o.uoff = make_float2(f[0][7], f[1][7]);
+  pairs[k] = o;
+}
+
+}  // namespace nlos

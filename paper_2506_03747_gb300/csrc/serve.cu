@@ -1,0 +1,890 @@
+// Serving: continuous batching of simulation requests on one GB300.
+//
+// Host side (C++): requests are queued by nlos_serve_submit; a scheduler
+// thread admits them first-in first-out while the device memory they hold
+// stays within the HBM budget, uploads their points and scan tables on a copy
+// stream, and publishes their work as items in a ring in mapped host memory:
+//   PREP    pack the points (ingest step) and zero the output cube,
+//   FORWARD pair-histogram units (scan tile, bin window, point block) with the
+//           fused jitter, exactly as the standalone forward kernel runs them,
+//   REDUCE  per-cube maximum and FP64 sums,
+//   NOISE   Philox/Poisson counts.
+// The next phase of a request is published when the device reports the
+// current one complete. Requests admitted while others run are interleaved
+// item by item on the device.
+//
+// Device side: one persistent kernel (one CTA per SM) claims items in order
+// from a device-side head counter once the host has published them (tail in
+// mapped memory), copies the item and its job descriptor into shared memory,
+// runs it and bumps the job's phase counter in mapped memory. Every wait is
+// bounded: an unpublished claimed item gives up after about a second and sets
+// an error word; an idle CTA exits after the host parks the queue (or after
+// about a second with nothing to do), and the host relaunches the kernel when
+// new work arrives. CTAs never wait for one another.
+#include "common.cuh"
+#include "device_util.cuh"
+#include "forward_core.cuh"
+#include "noise_core.cuh"
+#include "pack_core.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace nlos {
+
+nlos_status resolve_params(const nlos_params& p, uint64_t num_points, Geometry& g);
+void scan_points_host(const nlos_params& p, const Geometry& g, std::vector<ScanPoint>& out);
+
+namespace serve {
+
+enum ItemKind : uint32_t { K_PACK = 0, K_ZERO = 1, K_FWD = 2, K_REDUCE = 3, K_NOISE = 4 };
+enum Phase : int { PH_PREP = 0, PH_FWD = 1, PH_REDUCE = 2, PH_NOISE = 3 };
+__host__ __device__ inline int phase_of(uint32_t kind) {
+  return kind <= K_ZERO ? PH_PREP : kind == K_FWD ? PH_FWD : kind == K_REDUCE ? PH_REDUCE : PH_NOISE;
+}
+
+constexpr uint64_t kRing = 1ull << 16;      // work-item ring slots
+constexpr int kMaxJobs = 1024;               // concurrently admitted requests
+constexpr uint32_t kCapBw = 1024;            // histogram bins per window in the serving kernel
+constexpr uint32_t kPackChunk = 16384;       // pairs per PACK item
+constexpr uint64_t kZeroChunk = 1ull << 20;  // floats per ZERO item
+constexpr uint32_t kFwdChunk = 16;           // point blocks per FORWARD item
+constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
+constexpr uint64_t kNoiseChunk = 1ull << 18; // bins per NOISE item
+constexpr long long kIdleCycles = 2000000000LL;  // ~1 s without work: exit
+constexpr int kServeThreads = 768;            // 24 warps: no register spills in the fused paths
+constexpr uint64_t kNone = ~0ull;
+constexpr uint64_t kSkip = ~0ull - 1;
+
+struct __align__(16) JobDesc {
+  FwdArgs fwd;               // forward arguments (tau, pairs, scan, taps, ...)
+  const float* raw;          // [P][8] uploaded points
+  uint32_t* counts;          // [S][B] or null
+  SceneScratch* scratch;     // device
+  uint64_t P, S, n;          // points, scan points, bins in the cube
+  int scan_mode, cos_mode, bin_mode, noise_mode;
+  double lx, ly, inv_cdt;
+  float peak_photons, dark, nr_db, pad0;
+  uint64_t seed;
+  uint32_t tag, pad1, pad2, pad3;
+};
+static_assert(sizeof(JobDesc) % 16 == 0, "JobDesc copies as int4");
+
+struct __align__(32) WorkItem {
+  uint32_t job;
+  uint32_t kind;
+  uint64_t begin, end;
+  uint64_t seq;  // == ring index once the slot is published
+};
+
+struct Control {
+  uint64_t tail;       // items published (host)
+  uint64_t completed;  // items finished or skipped (device)
+  uint64_t err_item;   // ring index of an item whose publication wait gave up
+  uint32_t park;       // host: idle CTAs may exit
+  uint32_t err;        // device: kErr* bits
+  int32_t alive;       // device: CTAs running
+  uint32_t pad[7];
+};
+
+struct JobStatus {
+  uint32_t done[4];    // items finished per phase
+};
+
+struct ServeArgs {
+  Control* ctl;        // mapped
+  WorkItem* ring;      // mapped [kRing]
+  JobDesc* jobs;       // mapped [kMaxJobs]
+  JobStatus* status;   // mapped [kMaxJobs]
+  unsigned long long* head;  // device
+};
+
+__device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+template <int SCAN, int COS>
+__device__ bool fwd_item_mode(const FwdArgs& a, uint64_t b, uint64_t e, const FwdSmem& sm,
+                              uint32_t& it, int bin_mode) {
+  unsigned long long nb = 0;
+  if (bin_mode == NLOS_BIN_SPLAT) return fwd_run<SCAN, COS, MODE_SPLAT>(a, b, e, sm, it, nb);
+  return fwd_run<SCAN, COS, MODE_NEAREST>(a, b, e, sm, it, nb);
+}
+
+__device__ bool fwd_item(const JobDesc& j, uint64_t b, uint64_t e, const FwdSmem& sm,
+                         uint32_t& it) {
+  const FwdArgs& a = j.fwd;
+  if (j.scan_mode == NLOS_CONFOCAL) {
+    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_mode<NLOS_CONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, j.bin_mode);
+    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, j.bin_mode);
+    return fwd_item_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, j.bin_mode);
+  }
+  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_mode<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, j.bin_mode);
+  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, j.bin_mode);
+  return fwd_item_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, j.bin_mode);
+}
+
+// REDUCE: transients [b, e) of the job, one warp per transient; the cube's
+// maximum and FP64 sums go to the job's scratch.
+__device__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t e) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t B = j.fwd.B;
+  double csum = 0.0, csq = 0.0;
+  float cmax = 0.0f;
+  for (uint64_t t = b + warp; t < e; t += nwarps) {
+    const float* row = j.fwd.tau + t * B;
+    double s = 0.0, q = 0.0;
+    float m = 0.0f;
+    for (uint32_t i = lane; i < B; i += 32) {
+      const float v = row[i];
+      s += (double)v;
+      q += (double)v * v;
+      m = fmaxf(m, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    csum += s;
+    csq += q;
+    cmax = fmaxf(cmax, m);
+  }
+  if (lane == 0) {
+    atomicMax(&j.scratch->peak_bits, __float_as_uint(cmax));
+    atomicAdd(&j.scratch->sum, csum);
+    atomicAdd(&j.scratch->sumsq, csq);
+  }
+}
+
+// NOISE: bins [b, e) of the job; scale from the job's reduction.
+__device__ void noise_item(const JobDesc& j, uint64_t b, uint64_t e) {
+  const float scale = noise_scale_from(j.scratch, j.noise_mode, j.peak_photons, j.nr_db, j.n);
+  if (b == 0 && threadIdx.x == 0) {
+    j.scratch->scale = scale;
+    j.scratch->dark = j.dark;
+  }
+  for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    const float lam = fmaf(scale, j.fwd.tau[i], j.dark);
+    j.counts[i] = poisson_sample(lam, i, j.seed, j.tag);
+  }
+}
+
+__global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs q) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  FwdSmem sm;
+  sm.hist = reinterpret_cast<float*>(smem);
+  sm.stage = reinterpret_cast<PointPair*>(smem + (size_t)kCapBw * kTile * 4);
+  sm.bars = reinterpret_cast<uint64_t*>(sm.stage + 2 * kPairsPerBlock);
+  JobDesc* jd = reinterpret_cast<JobDesc*>(sm.bars + 2);
+  __shared__ WorkItem s_item;
+  __shared__ unsigned long long s_idx;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&sm.bars[0], 1);
+    mbar_init(&sm.bars[1], 1);
+    fence_mbar_init();
+    atomicAdd_system(&q.ctl->alive, 1);
+  }
+  __syncthreads();
+  uint32_t it = 0;
+
+  for (;;) {
+    if (tid == 0) {
+      unsigned long long got = kNone;
+      const long long t0 = clock64();
+      for (;;) {
+        const uint64_t tail = ld_acquire_sys(&q.ctl->tail);
+        const unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(q.head);
+        if (h < tail) {
+          if (atomicCAS(q.head, h, h + 1) == h) {
+            got = h;
+            break;
+          }
+          continue;
+        }
+        if (ld_volatile_u32(&q.ctl->park)) break;
+        if (clock64() - t0 > kIdleCycles) break;
+        __nanosleep(500);
+      }
+      if (got != kNone) {
+        // the slot is written before the tail moves; a withheld publication
+        // leaves a stale sequence number: wait (bounded), then give up
+        WorkItem* slot = q.ring + (got % kRing);
+        const long long t1 = clock64();
+        while (ld_acquire_sys(&slot->seq) != got) {
+          if (clock64() - t1 > kWaitCycles) {
+            atomicOr_system(&q.ctl->err, kErrWaitTimeout);
+            atomicExch(reinterpret_cast<unsigned long long*>(&q.ctl->err_item), got);
+            got = kSkip;
+            break;
+          }
+          __nanosleep(200);
+        }
+        if (got != kSkip) s_item = *slot;
+      }
+      s_idx = got;
+    }
+    __syncthreads();
+    const unsigned long long idx = s_idx;
+    if (idx == kNone) break;
+    if (idx == kSkip) {
+      if (tid == 0) {
+        __threadfence_system();
+        atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed), 1ull);
+      }
+      __syncthreads();
+      continue;
+    }
+    const WorkItem item = s_item;
+    // job descriptor: mapped memory -> shared memory
+    {
+      const int4* src = reinterpret_cast<const int4*>(q.jobs + item.job);
+      int4* dst = reinterpret_cast<int4*>(jd);
+      for (int i = tid; i < (int)(sizeof(JobDesc) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    bool ok = true;
+    switch (item.kind) {
+      case K_PACK:
+        for (uint64_t k = item.begin + tid; k < item.end; k += blockDim.x)
+          pack_pair(jd->raw, jd->P, k, jd->scan_mode, jd->cos_mode, jd->lx, jd->ly, jd->inv_cdt,
+                    const_cast<PointPair*>(jd->fwd.pairs), &jd->scratch->err);
+        break;
+      case K_ZERO:
+        for (uint64_t k = item.begin + tid; k < item.end; k += blockDim.x) jd->fwd.tau[k] = 0.0f;
+        break;
+      case K_FWD:
+        ok = fwd_item(*jd, item.begin, item.end, sm, it);
+        break;
+      case K_REDUCE:
+        reduce_item(*jd, item.begin, item.end);
+        break;
+      default:
+        noise_item(*jd, item.begin, item.end);
+        break;
+    }
+    (void)ok;  // a forward wait that gave up is recorded in the job error word
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence_system();
+      atomicAdd_system(&q.status[item.job].done[phase_of(item.kind)], 1u);
+      atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed), 1ull);
+    }
+  }
+  if (tid == 0) atomicSub_system(&q.ctl->alive, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Host scheduler.
+// ---------------------------------------------------------------------------
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { R_PENDING, R_UPLOAD, R_RUNNING, R_DRAINING, R_FINISHING, R_DONE, R_FAILED, R_CANCELLED };
+
+struct Request {
+  uint64_t ticket = 0;
+  nlos_params params{};
+  Geometry g{};
+  std::vector<float> pts;
+  ReqState state = R_PENDING;
+  nlos_status status = NLOS_OK;
+  std::string msg;
+  int slot = -1;
+  char* dev = nullptr;
+  size_t bytes = 0;
+  PointPair* pairs = nullptr;
+  float* raw = nullptr;
+  ScanPoint* scan = nullptr;
+  float* tau = nullptr;
+  uint32_t* counts = nullptr;
+  SceneScratch* scratch = nullptr;
+  SceneScratch* h_scratch = nullptr;  // pinned copy at completion
+  cudaEvent_t ev = nullptr;
+  int phase = 0;
+  uint32_t items[4] = {0, 0, 0, 0};
+  uint32_t withheld = 0;  // published items that will never complete (fault injection)
+  uint64_t first_item = 0, last_item = 0;
+  bool release_on_done = false;
+  Clock::time_point t_submit, t_done;
+  nlos_stats stats{};
+};
+
+struct Server {
+  uint64_t budget = 0, resident = 0;
+  std::mutex mu;
+  std::condition_variable cv_done, cv_work;
+  std::deque<Request*> pending;
+  std::unordered_map<uint64_t, Request*> reqs;
+  std::vector<Request*> active;
+  std::vector<int> free_slots;
+  std::thread th;
+  std::atomic<bool> stop{false};
+  uint64_t next_ticket = 1;
+  int device = 0, num_sms = 0;
+  cudaStream_t kstream = nullptr, cstream = nullptr;
+  Control* ctl = nullptr;
+  WorkItem* ring = nullptr;
+  JobDesc* jobs = nullptr;
+  JobStatus* status = nullptr;
+  unsigned long long* d_head = nullptr;
+  uint64_t published = 0;
+  bool kernel_running = false;
+  cudaEvent_t kernel_done = nullptr;
+  size_t smem = 0;
+  // fault injection (tests)
+  int inject = 0;
+  uint64_t withheld_item = kNone;
+  Request* withheld_req = nullptr;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+
+void carve(Request* r) {
+  const Geometry& g = r->g;
+  const uint64_t n_pairs = (g.P + 1) / 2;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  size_t o_pairs = take(sizeof(PointPair) * (n_pairs ? n_pairs : 1));
+  size_t o_raw = take(sizeof(float) * 8 * (g.P ? g.P : 1));
+  size_t o_scan = take(sizeof(ScanPoint) * g.S);
+  size_t o_tau = take(sizeof(float) * g.S * g.B);
+  size_t o_cnt = g.noise_mode != NLOS_NOISE_NONE ? take(sizeof(uint32_t) * g.S * g.B) : 0;
+  size_t o_scr = take(sizeof(SceneScratch));
+  r->bytes = off;
+  if (!r->dev) return;
+  r->pairs = reinterpret_cast<PointPair*>(r->dev + o_pairs);
+  r->raw = reinterpret_cast<float*>(r->dev + o_raw);
+  r->scan = reinterpret_cast<ScanPoint*>(r->dev + o_scan);
+  r->tau = reinterpret_cast<float*>(r->dev + o_tau);
+  r->counts = g.noise_mode != NLOS_NOISE_NONE ? reinterpret_cast<uint32_t*>(r->dev + o_cnt) : nullptr;
+  r->scratch = reinterpret_cast<SceneScratch*>(r->dev + o_scr);
+}
+
+void fill_job(Server& sv, Request* r, JobDesc& j) {
+  std::memset(&j, 0, sizeof(j));
+  const Geometry& g = r->g;
+  const nlos_params& p = r->params;
+  FwdArgs& a = j.fwd;
+  a.pairs = r->pairs;
+  a.scan = r->scan;
+  a.tau = r->tau;
+  a.err = &r->scratch->err;
+  a.boundary = &r->scratch->boundary_pairs;
+  a.n_pairs = (uint32_t)((g.P + 1) / 2);
+  a.S = (uint32_t)g.S;
+  a.B = g.B;
+  a.kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
+  a.ppb = kPairsPerBlock;
+  a.n_win = (g.B + kCapBw - 1) / kCapBw;
+  a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
+  a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
+  a.units = (unsigned long long)((g.S + kTile - 1) / kTile) * a.n_win * a.n_blk;
+  if (g.bin_mode == NLOS_BIN_SPLAT) {
+    const double s = g.sigma;
+    a.inv2s2 = (float)(1.0 / (2.0 * s * s));
+    a.norm = (float)(1.0 / (s * std::sqrt(2.0 * 3.14159265358979323846)));
+    a.reach = (float)(6.0 * s);
+    a.qstep = (float)std::exp(-1.0 / (s * s));
+    a.R = 0;
+    a.taps[0] = 1.0f;
+  } else {
+    a.R = (jitter_taps(g.sigma, a.taps, kMaxTaps) - 1) / 2;
+  }
+  j.raw = r->raw;
+  j.counts = r->counts;
+  j.scratch = r->scratch;
+  j.P = g.P;
+  j.S = g.S;
+  j.n = g.S * (uint64_t)g.B;
+  j.scan_mode = g.scan_mode;
+  j.cos_mode = g.cos_mode;
+  j.bin_mode = g.bin_mode;
+  j.noise_mode = g.noise_mode;
+  j.lx = p.laser_x;
+  j.ly = p.laser_y;
+  j.inv_cdt = 1.0 / g.cdt;
+  j.peak_photons = p.peak_photons;
+  j.dark = p.dark_per_bin;
+  j.nr_db = p.nr_db;
+  j.seed = p.seed;
+  j.tag = p.stream_tag;
+  (void)sv;
+}
+
+// Writes items into the ring and moves the tail (release).
+void publish(Server& sv, Request* r, std::vector<WorkItem>& items) {
+  // keep fewer than half the ring outstanding (see the claim protocol)
+  while (sv.published + items.size() - __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE) >=
+         kRing / 2)
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  uint64_t idx = sv.published;
+  for (WorkItem& w : items) {
+    WorkItem* slot = sv.ring + (idx % kRing);
+    slot->job = w.job;
+    slot->kind = w.kind;
+    slot->begin = w.begin;
+    slot->end = w.end;
+    if (sv.inject == 1 && sv.withheld_item == kNone) {
+      // fault injection: the slot of this item is never published
+      sv.withheld_item = idx;
+      sv.withheld_req = r;
+      r->withheld += 1;
+      sv.inject = 0;
+    } else {
+      __atomic_store_n(&slot->seq, idx, __ATOMIC_RELEASE);
+    }
+    ++idx;
+  }
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  __atomic_store_n(&sv.ctl->tail, idx, __ATOMIC_RELEASE);
+  r->last_item = idx;
+  sv.published = idx;
+}
+
+void publish_phase(Server& sv, Request* r, int phase) {
+  const Geometry& g = r->g;
+  std::vector<WorkItem> items;
+  const uint32_t job = (uint32_t)r->slot;
+  if (phase == PH_PREP) {
+    const uint64_t n_pairs = (g.P + 1) / 2;
+    for (uint64_t b = 0; b < n_pairs; b += kPackChunk)
+      items.push_back({job, K_PACK, b, std::min<uint64_t>(n_pairs, b + kPackChunk), 0});
+    const uint64_t n = g.S * (uint64_t)g.B;
+    for (uint64_t b = 0; b < n; b += kZeroChunk)
+      items.push_back({job, K_ZERO, b, std::min<uint64_t>(n, b + kZeroChunk), 0});
+  } else if (phase == PH_FWD) {
+    const FwdArgs& a = sv.jobs[job].fwd;
+    const uint64_t tws = a.units / a.n_blk;
+    for (uint64_t tw = 0; tw < tws; ++tw)
+      for (uint64_t b = 0; b < a.n_blk; b += kFwdChunk)
+        items.push_back({job, K_FWD, tw * a.n_blk + b, tw * a.n_blk + std::min<uint64_t>(a.n_blk, b + kFwdChunk), 0});
+  } else if (phase == PH_REDUCE) {
+    for (uint64_t b = 0; b < g.S; b += kReduceChunk)
+      items.push_back({job, K_REDUCE, b, std::min<uint64_t>(g.S, b + kReduceChunk), 0});
+  } else {
+    const uint64_t n = g.S * (uint64_t)g.B;
+    for (uint64_t b = 0; b < n; b += kNoiseChunk)
+      items.push_back({job, K_NOISE, b, std::min<uint64_t>(n, b + kNoiseChunk), 0});
+  }
+  r->phase = phase;
+  r->items[phase] = (uint32_t)items.size();
+  if (items.empty()) return;
+  publish(sv, r, items);
+}
+
+void finish(Server& sv, Request* r, nlos_status st, const std::string& msg) {
+  r->status = st;
+  r->msg = msg;
+  r->state = st == NLOS_OK ? R_DONE : R_FAILED;
+  r->t_done = Clock::now();
+  (void)sv;
+}
+
+void free_request_memory(Server& sv, Request* r) {
+  if (r->dev) {
+    cudaFreeAsync(r->dev, sv.cstream);
+    sv.resident -= r->bytes;
+    r->dev = nullptr;
+  }
+  if (r->slot >= 0) {
+    sv.free_slots.push_back(r->slot);
+    r->slot = -1;
+  }
+}
+
+void destroy_request(Server& sv, Request* r) {
+  free_request_memory(sv, r);
+  if (r->ev) cudaEventDestroy(r->ev);
+  if (r->h_scratch) cudaFreeHost(r->h_scratch);
+  sv.reqs.erase(r->ticket);
+  delete r;
+}
+
+// One scheduler pass (called with the lock held).
+bool step(Server& sv) {
+  bool busy = false;
+  // admission, first-in first-out within the budget
+  while (!sv.pending.empty() && !sv.free_slots.empty()) {
+    Request* r = sv.pending.front();
+    carve(r);
+    if (r->bytes > sv.budget) {
+      sv.pending.pop_front();
+      finish(sv, r, NLOS_ENOMEM, "request needs more device memory than the server budget");
+      continue;
+    }
+    if (sv.resident + r->bytes > sv.budget) break;
+    sv.pending.pop_front();
+    if (sv.inject == 2) {
+      sv.inject = 0;
+      finish(sv, r, NLOS_ENOMEM, "device allocation refused (injected)");
+      continue;
+    }
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, sv.cstream);
+    if (e != cudaSuccess) {
+      r->dev = nullptr;
+      finish(sv, r, NLOS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+      continue;
+    }
+    sv.resident += r->bytes;
+    carve(r);
+    r->slot = sv.free_slots.back();
+    sv.free_slots.pop_back();
+    std::memset(&sv.status[r->slot], 0, sizeof(JobStatus));
+    // uploads on the copy stream (copy engines only: the serving kernel may be
+    // occupying every SM)
+    std::vector<ScanPoint> hs;
+    nlos::scan_points_host(r->params, r->g, hs);
+    SceneScratch zero{};
+    e = cudaMemcpyAsync(r->scan, hs.data(), sizeof(ScanPoint) * r->g.S, cudaMemcpyHostToDevice, sv.cstream);
+    if (e == cudaSuccess && r->g.P)
+      e = cudaMemcpyAsync(r->raw, r->pts.data(), sizeof(float) * 8 * r->g.P, cudaMemcpyHostToDevice, sv.cstream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->scratch, &zero, sizeof(zero), cudaMemcpyHostToDevice, sv.cstream);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev, sv.cstream);
+    if (e != cudaSuccess) {
+      free_request_memory(sv, r);
+      finish(sv, r, NLOS_ECUDA, cudaGetErrorString(e));
+      continue;
+    }
+    r->state = R_UPLOAD;
+    sv.active.push_back(r);
+    busy = true;
+  }
+  // progress of admitted requests
+  const uint32_t dev_err = __atomic_load_n(&sv.ctl->err, __ATOMIC_ACQUIRE);
+  for (size_t i = 0; i < sv.active.size();) {
+    Request* r = sv.active[i];
+    bool leave = false;
+    if (r->state == R_UPLOAD) {
+      if (cudaEventQuery(r->ev) == cudaSuccess) {
+        r->pts.clear();
+        r->pts.shrink_to_fit();
+        fill_job(sv, r, sv.jobs[r->slot]);
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        r->state = R_RUNNING;
+        publish_phase(sv, r, PH_PREP);
+        busy = true;
+      }
+    } else if (r->state == R_RUNNING) {
+      if (sv.withheld_req == r && (dev_err & kErrWaitTimeout)) {
+        // the device gave up on the withheld item: the request cannot finish;
+        // its memory stays until every other item published for it is done
+        sv.withheld_req = nullptr;
+        r->state = R_DRAINING;
+        r->status = NLOS_ETIMEOUT;
+        r->msg = "a work item was never published; the device wait gave up";
+        busy = true;
+      } else {
+        const uint32_t done = __atomic_load_n(&sv.status[r->slot].done[r->phase], __ATOMIC_ACQUIRE);
+        if (done >= r->items[r->phase]) {
+          int next = r->phase + 1;
+          if (next == PH_NOISE && r->g.noise_mode == NLOS_NOISE_NONE) next = 4;
+          if (next <= PH_NOISE) {
+            publish_phase(sv, r, next);
+          } else {
+            cudaMemcpyAsync(r->h_scratch, r->scratch, sizeof(SceneScratch), cudaMemcpyDeviceToHost, sv.cstream);
+            cudaEventRecord(r->ev, sv.cstream);
+            r->state = R_FINISHING;
+          }
+          busy = true;
+        }
+      }
+    } else if (r->state == R_DRAINING) {
+      uint32_t done = 0, total = 0;
+      for (int ph = 0; ph <= r->phase; ++ph) {
+        done += __atomic_load_n(&sv.status[r->slot].done[ph], __ATOMIC_ACQUIRE);
+        total += r->items[ph];
+      }
+      if (done + r->withheld >= total) {
+        r->state = R_FAILED;
+        r->t_done = Clock::now();
+        leave = true;
+      }
+    } else if (r->state == R_FINISHING) {
+      if (cudaEventQuery(r->ev) == cudaSuccess) {
+        const SceneScratch& h = *r->h_scratch;
+        const uint64_t n = r->g.S * (uint64_t)r->g.B;
+        nlos_stats& s = r->stats;
+        s.struct_size = sizeof(nlos_stats);
+        s.pairs = r->g.S * r->g.P;
+        float peak;
+        std::memcpy(&peak, &h.peak_bits, sizeof(peak));
+        s.peak = peak;
+        s.mean = n ? h.sum / (double)n : 0.0;
+        s.variance = n ? std::max(0.0, h.sumsq / (double)n - s.mean * s.mean) : 0.0;
+        s.noise_scale = r->counts ? h.scale : 0.0;
+        s.noise_dark = r->counts ? h.dark : 0.0;
+        s.device_error = h.err;
+        if (h.err & kErrBadPoint) finish(sv, r, NLOS_EINVAL, "invalid surface point");
+        else if (h.err & kErrWaitTimeout) finish(sv, r, NLOS_ETIMEOUT, "a bounded device wait gave up");
+        else finish(sv, r, NLOS_OK, "");
+        leave = true;
+      }
+    }
+    if (leave) {
+      sv.active.erase(sv.active.begin() + i);
+      if (r->status != NLOS_OK) free_request_memory(sv, r);
+      if (r->release_on_done) destroy_request(sv, r);
+      sv.cv_done.notify_all();
+    } else {
+      ++i;
+    }
+  }
+  // kernel lifecycle: run while items are outstanding, park when idle
+  const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
+  if (sv.kernel_running && cudaEventQuery(sv.kernel_done) == cudaSuccess) sv.kernel_running = false;
+  if (sv.published > completed && !sv.kernel_running) {
+    __atomic_store_n(&sv.ctl->park, 0u, __ATOMIC_RELEASE);
+    ServeArgs q{sv.ctl, sv.ring, sv.jobs, sv.status, sv.d_head};
+    serve_kernel<<<sv.num_sms, kServeThreads, sv.smem, sv.kstream>>>(q);
+    cudaEventRecord(sv.kernel_done, sv.kstream);
+    sv.kernel_running = true;
+  }
+  if (sv.active.empty() && sv.pending.empty())
+    __atomic_store_n(&sv.ctl->park, 1u, __ATOMIC_RELEASE);
+  return busy || !sv.active.empty();
+}
+
+void run(Server* sv) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (!sv->stop.load()) {
+    const bool busy = step(*sv);
+    if (busy) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(10));
+      lk.lock();
+    } else {
+      sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    }
+  }
+}
+
+}  // namespace serve
+}  // namespace nlos
+
+struct nlos_server {
+  nlos::serve::Server sv;
+};
+
+using namespace nlos;
+using namespace nlos::serve;
+
+extern "C" {
+
+nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
+  clear_error();
+  if (!out) return set_error(NLOS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (hbm_budget_bytes == 0) return set_error(NLOS_EINVAL, "hbm_budget_bytes must be > 0");
+  nlos_server* s = new (std::nothrow) nlos_server();
+  if (!s) return set_error(NLOS_ENOMEM, "host allocation failed");
+  Server& sv = s->sv;
+  sv.budget = hbm_budget_bytes;
+  auto fail = [&](cudaError_t e, const char* what) {
+    if (sv.ctl) cudaFreeHost(sv.ctl);
+    if (sv.ring) cudaFreeHost(sv.ring);
+    if (sv.jobs) cudaFreeHost(sv.jobs);
+    if (sv.status) cudaFreeHost(sv.status);
+    if (sv.d_head) cudaFree(sv.d_head);
+    delete s;
+    return cuda_error(e, what);
+  };
+  cudaError_t e = cudaGetDevice(&sv.device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sv.num_sms, cudaDevAttrMultiProcessorCount, sv.device);
+  if (e != cudaSuccess) return fail(e, "cudaGetDevice");
+  const unsigned flags = cudaHostAllocMapped | cudaHostAllocPortable;
+  if ((e = cudaHostAlloc(&sv.ctl, sizeof(Control), flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
+  if ((e = cudaHostAlloc(&sv.ring, sizeof(WorkItem) * kRing, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
+  if ((e = cudaHostAlloc(&sv.jobs, sizeof(JobDesc) * kMaxJobs, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
+  if ((e = cudaHostAlloc(&sv.status, sizeof(JobStatus) * kMaxJobs, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
+  std::memset(sv.ctl, 0, sizeof(Control));
+  std::memset(sv.ring, 0xff, sizeof(WorkItem) * kRing);  // seq = ~0: unpublished
+  std::memset(sv.jobs, 0, sizeof(JobDesc) * kMaxJobs);
+  std::memset(sv.status, 0, sizeof(JobStatus) * kMaxJobs);
+  if ((e = cudaMalloc(&sv.d_head, sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMemset(sv.d_head, 0, sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMemset");
+  if ((e = cudaStreamCreateWithFlags(&sv.kstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
+  if ((e = cudaStreamCreateWithFlags(&sv.cstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&sv.kernel_done, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "cudaEventCreate");
+  sv.smem = (size_t)kCapBw * kTile * 4 + 2 * (size_t)kPairsPerBlock * sizeof(PointPair) + 16 + sizeof(JobDesc) + 64;
+  if ((e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv.smem)) != cudaSuccess)
+    return fail(e, "cudaFuncSetAttribute");
+  cudaDeviceSynchronize();
+  for (int i = kMaxJobs - 1; i >= 0; --i) sv.free_slots.push_back(i);
+  sv.th = std::thread(run, &sv);
+  *out = s;
+  return NLOS_OK;
+}
+
+nlos_status nlos_serve_submit(nlos_server* server, const nlos_params* params,
+                              const float* points_aos8, uint64_t num_points, uint64_t* ticket_out) {
+  clear_error();
+  if (!server || !params || !ticket_out) return set_error(NLOS_EINVAL, "server, params and ticket_out must not be NULL");
+  if (num_points && !points_aos8) return set_error(NLOS_EINVAL, "points_aos8 is NULL");
+  Request* r = new (std::nothrow) Request();
+  if (!r) return set_error(NLOS_ENOMEM, "host allocation failed");
+  nlos_status st = resolve_params(*params, num_points, r->g);
+  if (st != NLOS_OK) {
+    delete r;
+    return st;
+  }
+  r->params = *params;
+  if (r->g.bin_mode == NLOS_BIN_NEAREST && jitter_radius(r->g.sigma) > 64) {
+    delete r;
+    return set_error(NLOS_EINVAL, "jitter too wide");
+  }
+  try {
+    r->pts.assign(points_aos8, points_aos8 + 8 * num_points);
+  } catch (...) {
+    delete r;
+    return set_error(NLOS_ENOMEM, "host allocation failed");
+  }
+  if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaHostAlloc(&r->h_scratch, sizeof(SceneScratch), cudaHostAllocDefault) != cudaSuccess) {
+    if (r->ev) cudaEventDestroy(r->ev);
+    delete r;
+    return set_error(NLOS_ECUDA, "event or pinned allocation failed");
+  }
+  Server& sv = server->sv;
+  {
+    std::lock_guard<std::mutex> lk(sv.mu);
+    r->ticket = sv.next_ticket++;
+    r->t_submit = Clock::now();
+    sv.reqs[r->ticket] = r;
+    sv.pending.push_back(r);
+  }
+  sv.cv_work.notify_one();
+  *ticket_out = r->ticket;
+  return NLOS_OK;
+}
+
+nlos_status nlos_serve_poll(nlos_server* server, uint64_t ticket, int wait_ms,
+                            const float** tau_dev_out, const uint32_t** counts_dev_out,
+                            nlos_stats* stats) {
+  clear_error();
+  if (!server) return set_error(NLOS_EINVAL, "server is NULL");
+  if (stats && stats->struct_size != sizeof(nlos_stats))
+    return set_error(NLOS_EINVAL, "nlos_stats.struct_size does not match this library");
+  Server& sv = server->sv;
+  std::unique_lock<std::mutex> lk(sv.mu);
+  auto it = sv.reqs.find(ticket);
+  if (it == sv.reqs.end()) return set_error(NLOS_ENOTFOUND, "unknown ticket");
+  Request* r = it->second;
+  auto finished = [&] { return r->state == R_DONE || r->state == R_FAILED || r->state == R_CANCELLED; };
+  if (!finished() && wait_ms > 0)
+    sv.cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), finished);
+  if (!finished()) return set_error(NLOS_EBUSY, "pending");
+  if (r->state == R_CANCELLED) return set_error(NLOS_ECANCELLED, "cancelled");
+  if (r->state == R_FAILED) return set_error(r->status, r->msg);
+  if (tau_dev_out) *tau_dev_out = r->tau;
+  if (counts_dev_out) *counts_dev_out = r->counts;
+  if (stats) *stats = r->stats;
+  return NLOS_OK;
+}
+
+nlos_status nlos_serve_release(nlos_server* server, uint64_t ticket) {
+  clear_error();
+  if (!server) return set_error(NLOS_EINVAL, "server is NULL");
+  Server& sv = server->sv;
+  std::lock_guard<std::mutex> lk(sv.mu);
+  auto it = sv.reqs.find(ticket);
+  if (it == sv.reqs.end()) return set_error(NLOS_ENOTFOUND, "unknown ticket");
+  Request* r = it->second;
+  if (r->state == R_PENDING) {
+    sv.pending.erase(std::find(sv.pending.begin(), sv.pending.end(), r));
+    destroy_request(sv, r);
+  } else if (r->state == R_DONE || r->state == R_FAILED || r->state == R_CANCELLED) {
+    destroy_request(sv, r);
+  } else {
+    // admitted: the ticket is gone now; the memory is freed once the work
+    // already published for it has completed on the device
+    r->release_on_done = true;
+    sv.reqs.erase(it);
+  }
+  return NLOS_OK;
+}
+
+nlos_status nlos_server_destroy(nlos_server* server) {
+  clear_error();
+  if (!server) return set_error(NLOS_EINVAL, "server is NULL");
+  Server& sv = server->sv;
+  {
+    // let admitted work finish (bounded), then park the kernel
+    auto t0 = Clock::now();
+    std::unique_lock<std::mutex> lk(sv.mu);
+    while (!sv.active.empty() && Clock::now() - t0 < std::chrono::seconds(30)) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::milliseconds(1));
+      lk.lock();
+    }
+    for (Request* r : sv.pending) r->state = R_CANCELLED;
+    sv.pending.clear();
+    __atomic_store_n(&sv.ctl->park, 1u, __ATOMIC_RELEASE);
+  }
+  sv.stop.store(true);
+  sv.cv_work.notify_all();
+  if (sv.th.joinable()) sv.th.join();
+  cudaStreamSynchronize(sv.kstream);  // the kernel exits once parked (bounded waits)
+  cudaStreamSynchronize(sv.cstream);
+  std::vector<Request*> all;
+  for (auto& kv : sv.reqs) all.push_back(kv.second);
+  for (Request* r : all) destroy_request(sv, r);
+  cudaStreamSynchronize(sv.cstream);
+  cudaEventDestroy(sv.kernel_done);
+  cudaStreamDestroy(sv.kstream);
+  cudaStreamDestroy(sv.cstream);
+  cudaFree(sv.d_head);
+  cudaFreeHost(sv.ctl);
+  cudaFreeHost(sv.ring);
+  cudaFreeHost(sv.jobs);
+  cudaFreeHost(sv.status);
+  delete server;
+  return NLOS_OK;
+}
+
+nlos_status nlos_server_inject(nlos_server* server, int fault) {
+  clear_error();
+  if (!server) return set_error(NLOS_EINVAL, "server is NULL");
+  if (fault < 0 || fault > 2) return set_error(NLOS_EINVAL, "unknown fault");
+  std::lock_guard<std::mutex> lk(server->sv.mu);
+  server->sv.inject = fault;
+  return NLOS_OK;
+}
+
+nlos_status nlos_server_stats(nlos_server* server, uint64_t* resident_bytes, uint32_t* pending,
+                              uint32_t* active) {
+  clear_error();
+  if (!server) return set_error(NLOS_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(server->sv.mu);
+  if (resident_bytes) *resident_bytes = server->sv.resident;
+  if (pending) *pending = (uint32_t)server->sv.pending.size();
+  if (active) *active = (uint32_t)server->sv.active.size();
+  return NLOS_OK;
+}
+
+}  // extern "C"

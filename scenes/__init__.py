@@ -184,10 +184,14 @@ def primitive_union_points(rng, n_points: int):
 
 
 def workload_union64(seed: int = SEED_BASE + 2, n_points: int = 262144):
+    """The acquisition window starts at the earliest object round trip seen
+    from the wall centre (2 * stand-off + 2 * 0.3 m), so that it covers the
+    nearest part of the scene."""
     rng = np.random.default_rng(seed)
     params = default_params(scan_nx=64, scan_ny=64, wall_half_x=1.0, wall_half_y=1.0,
                             bin_width_s=8e-12, num_bins=512, standoff_m=1.0,
-                            standoff_mode="euclidean", jitter_fwhm_s=60e-12,
+                            standoff_mode="euclidean", window_start_m=2.0 * 1.0 + 2.0 * 0.3,
+                            jitter_fwhm_s=60e-12,
                             noise_mode="peak", peak_photons=100.0, dark_per_bin=1e-3,
                             seed=seed)
     pts, _ = primitive_union_points(rng, n_points)
@@ -222,11 +226,13 @@ def heightfield_points(rng, n: int, half: float = 1.0, z_lo: float = 0.4, z_hi: 
 
 
 def workload_heightfield128(seed: int = SEED_BASE + 3, n_side: int = 1024):
+    """Window from the earliest round trip at the wall centre (2 * 1.5 + 2 * 0.4 m)."""
     rng = np.random.default_rng(seed)
     params = default_params(scan_nx=128, scan_ny=128, wall_half_x=1.0, wall_half_y=1.0,
                             scan_mode="nonconfocal", laser_xy=(0.0, 0.0),
                             bin_width_s=4e-12, num_bins=1024, standoff_m=1.5,
-                            standoff_mode="euclidean", jitter_fwhm_s=30e-12,
+                            standoff_mode="euclidean", window_start_m=2.0 * 1.5 + 2.0 * 0.4,
+                            jitter_fwhm_s=30e-12,
                             noise_mode="peak", peak_photons=100.0, dark_per_bin=1e-3,
                             seed=seed)
     pts = heightfield_points(rng, n_side)
@@ -288,6 +294,7 @@ def serving_trace(n_requests: int = 2000, rate_hz: float = 200.0, seed: int = SE
                                 scan_mode="confocal" if confocal else "nonconfocal",
                                 bin_width_s=dt, num_bins=bins, standoff_m=1.0,
                                 standoff_mode="euclidean",
+                                window_start_m=2.0 + 2.0 * (0.3 if kind == "union" else 0.4),
                                 jitter_fwhm_s=fwhm, noise_mode="peak", peak_photons=100.0,
                                 dark_per_bin=1e-3, seed=rid)
         reqs.append(dict(id=rid, arrival_s=t, params=params, kind=kind, n_points=npts,

@@ -1,0 +1,154 @@
+"""GPU parity of the detector steps through the C ABI: Philox words
+(bit-exact), the standalone jitter kernel, the FP64 reductions, the Poisson
+sampler on identical expected counts (all but a handful of bins equal; the
+rest differ only where the device and host exp/log/lgamma round differently),
+and the noise of the whole pipeline (statistically)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def test_philox_words_bit_exact():
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(123)
+    n = 1 << 20
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:16] = 0
+    ctr[16:32, 0] = np.arange(16)
+    for key in [(0, 0), (0xDEADBEEF, 0x12345678), (0xFFFFFFFF, 0xFFFFFFFF)]:
+        c = torch.from_numpy(ctr.view(np.int32)).cuda()
+        out = torch.empty_like(c)
+        nlos.philox(c, n, key[0], key[1], out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32)
+        sel = rng.choice(n, size=4096, replace=False)
+        sel = np.r_[np.arange(32), sel]
+        np.testing.assert_array_equal(got[sel], oracle.philox(ctr[sel], key))
+
+
+def test_jitter_kernel_matches_oracle():
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(5)
+    for traces, B, fwhm, dt in [(37, 512, 60e-12, 8e-12), (5, 3001, 70e-12, 4e-12),
+                                (3, 100, 0.0, 8e-12), (2, 8, 200e-12, 8e-12)]:
+        x = rng.random((traces, B)).astype(np.float32)
+        x[:, rng.random(B) < 0.5] = 0
+        xin = torch.from_numpy(x).cuda()
+        out = torch.empty_like(xin)
+        nlos.jitter(xin, out, traces, B, fwhm, dt)
+        torch.cuda.synchronize()
+        ref = oracle.jitter(x.astype(np.float64), oracle.jitter_taps(fwhm, dt))
+        H.check_bins(out.cpu().numpy().astype(np.float64), ref, rel=1e-6, what="jitter")
+
+
+def test_reduce_matches_fp64():
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(6)
+    for traces, B in [(1000, 512), (7, 1023), (1, 1)]:
+        x = (rng.random((traces, B)) ** 4).astype(np.float32)
+        t = torch.from_numpy(x).cuda()
+        en = torch.empty(traces, dtype=torch.float64, device="cuda")
+        st = torch.empty(3, dtype=torch.float64, device="cuda")
+        nlos.reduce(t, traces, B, en, st)
+        torch.cuda.synchronize()
+        x64 = x.astype(np.float64)
+        np.testing.assert_allclose(en.cpu().numpy(), x64.sum(axis=1), rtol=1e-12)
+        mx, s, sq = st.cpu().numpy()
+        assert mx == x.max()
+        assert s == pytest.approx(x64.sum(), rel=1e-12)
+        assert sq == pytest.approx((x64 ** 2).sum(), rel=1e-12)
+
+
+def test_poisson_sampler_matches_oracle_on_same_lambda():
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(7)
+    n = 1 << 20
+    tau = (rng.random(n) ** 3).astype(np.float32)
+    tau[rng.random(n) < 0.3] = 0.0
+    for scale, dark in [(100.0, 1e-3), (9.0, 0.0), (3000.0, 0.5)]:
+        t = torch.from_numpy(tau).cuda()
+        c = torch.empty(n, dtype=torch.int32, device="cuda")
+        nlos.noise(t, n, scale, dark, seed=0xABCDEF01234, stream_tag=7, index_base=1000, counts=c)
+        torch.cuda.synchronize()
+        got = c.cpu().numpy().view(np.uint32)
+        lam = oracle.lam_from(tau.astype(np.float64), np.float32(scale), np.float32(dark))
+        ref = oracle.poisson(lam, 1000, 0xABCDEF01234, 7)
+        diff = (got != ref).sum()
+        print("scale", scale, "bins differing:", diff, "of", n)
+        assert diff <= max(3, n // 100000)
+
+
+def test_noise_statistics_full_pipeline():
+    """Noise of the whole forward pass (workload 2 geometry, reduced point set):
+    per-bin mean and variance over R = 400 seeds equal lambda (z-tests with a
+    Bonferroni threshold), and the device's noise scale equals the oracle's."""
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    params, pts = scenes.workload_union64(n_points=8192)
+    params = dict(params, scan_nx=16, scan_ny=16)
+    R = 400
+    prm = nlos.params(params)
+    sc = nlos.scene_create(prm, pts)
+    S, B = sc.num_scan, sc.num_bins
+    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    acc = torch.zeros((S, B), dtype=torch.float64, device="cuda")
+    acc2 = torch.zeros((S, B), dtype=torch.float64, device="cuda")
+    cnt = torch.empty((S, B), dtype=torch.int32, device="cuda")
+    st = None
+    for r in range(R):
+        sc_r = nlos.scene_create(nlos.params(params, seed=1000 + r), pts)
+        st = nlos.simulate(sc_r, tau, cnt, None, stats=True)
+        x = cnt.double()
+        acc += x
+        acc2 += x * x
+        sc_r.destroy()
+    tau_g = tau.double().cpu().numpy()
+    lam = st["noise_scale"] * tau_g + st["noise_dark"]
+    mean = acc.cpu().numpy() / R
+    var = acc2.cpu().numpy() / R - mean ** 2
+    o = oracle.simulate(params, pts, with_noise=True)
+    assert st["noise_scale"] == pytest.approx(o["scale"], rel=1e-4)
+    sel = lam > 0.5
+    z = (mean[sel] - lam[sel]) / np.sqrt(lam[sel] / R)
+    from scipy.stats import norm
+    thr = norm.isf(1e-3 / (2 * sel.sum()))
+    print("max |z| mean", np.abs(z).max(), "thr", thr, "bins", sel.sum())
+    assert np.abs(z).max() < thr
+    # variance: sample variance of Poisson has sd ~ sqrt((lam + 2 lam^2) / R)
+    zv = (var[sel] * R / (R - 1) - lam[sel]) / np.sqrt((lam[sel] + 2 * lam[sel] ** 2) / R)
+    print("max |z| var", np.abs(zv).max())
+    assert np.abs(zv).max() < thr + 1.0
+    # dark-only bins: counts ~ Poisson(dark); the total over bins and seeds is
+    # Poisson(n * R * dark)
+    dark_bins = tau_g == 0
+    if dark_bins.any():
+        tot = mean[dark_bins].sum() * R
+        expect = dark_bins.sum() * R * st["noise_dark"]
+        assert abs(tot - expect) < 5 * np.sqrt(expect) + 1
+
+
+def test_pipeline_counts_match_oracle_bins():
+    """Counts of the whole pipeline against the oracle's sampler fed the GPU's
+    own expected counts (lambda = scale * tau_G + dark, rounded to float): the
+    RNG streams and the sampler agree bin for bin."""
+    params, pts = scenes.workload_union64(n_points=4096)
+    params = dict(params, scan_nx=24, scan_ny=20)
+    g = H.gpu_forward(params, pts, counts=True, stats=True)
+    lam = oracle.lam_from(g["tau"], np.float32(g["stats"]["noise_scale"]),
+                          np.float32(g["stats"]["noise_dark"]))
+    ref = oracle.poisson(lam, 0, params["seed"], params["stream_tag"])
+    diff = (g["counts"] != ref).sum()
+    print("pipeline counts differing:", diff, "of", ref.size)
+    assert diff <= max(3, ref.size // 100000)

@@ -1,0 +1,188 @@
+"""Serving through the C ABI: each request served in a mix of concurrent
+requests equals the same request simulated alone (per-bin tolerance on the
+noise-free transient; Poisson counts equal except where lambda differs in its
+last bits), admission respects the HBM budget, and host-injected faults
+(cancellation, refused allocation, a withheld work-item publication that the
+device's bounded wait turns into NLOS_ETIMEOUT) leave the server usable."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(n, seed=0, max_points=20000, max_side=40):
+    rng = np.random.default_rng(seed)
+    pool_u, _ = scenes.primitive_union_points(np.random.default_rng(seed + 1), max_points)
+    pool_h = scenes.heightfield_points(np.random.default_rng(seed + 2), 141)
+    out = []
+    for i in range(n):
+        side = int(rng.integers(8, max_side))
+        bins = int(rng.choice([256, 300, 512, 700, 1100, 2048]))
+        dt = float(rng.uniform(4e-12, 16e-12))
+        kind = "union" if rng.random() < 0.5 else "heightfield"
+        pool = pool_u if kind == "union" else pool_h
+        P = int(rng.integers(100, min(max_points, len(pool))))
+        pts = pool[:P].copy()
+        pts[:, 7] *= len(pool) / P
+        prm = scenes.default_params(
+            scan_nx=side, scan_ny=side + int(rng.integers(0, 3)), wall_half_x=1.0, wall_half_y=1.0,
+            scan_mode="confocal" if rng.random() < 0.5 else "nonconfocal",
+            cos_mode=str(rng.choice(["object", "none", "object_wall"])),
+            bin_width_s=dt, num_bins=bins, standoff_m=1.0, standoff_mode="euclidean",
+            window_start_m=2.0 + 2.0 * (0.3 if kind == "union" else 0.4),
+            jitter_fwhm_s=float(rng.uniform(30e-12, 70e-12)),
+            noise_mode="peak" if rng.random() < 0.8 else "none", seed=1000 + i)
+        if rng.random() < 0.15:
+            prm["bin_mode"] = "splat"
+            prm["noise_mode"] = "none"
+        out.append((prm, pts))
+    return out
+
+
+def _alone(prm, pts):
+    from paper_2506_03747_gb300 import nlos
+    sc = nlos.scene_create(nlos.params(prm), pts)
+    S, B = sc.num_scan, sc.num_bins
+    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    cnt = (torch.empty((S, B), dtype=torch.int32, device="cuda")
+           if prm["noise_mode"] != "none" else None)
+    st = nlos.simulate(sc, tau, cnt, None, stats=True)
+    torch.cuda.synchronize()
+    return tau.cpu().numpy(), (cnt.cpu().numpy().view(np.uint32) if cnt is not None else None), st
+
+
+class _DevView:
+    """A read-only view of server-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 3}
+
+
+def _fetch(ptr, shape, dtype):
+    typestr = {torch.float32: "<f4", torch.int32: "<i4"}[dtype]
+    t = torch.as_tensor(_DevView(ptr, shape, typestr), device="cuda").clone()
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _wait(srv, ticket, timeout_s=60.0):
+    from paper_2506_03747_gb300 import nlos
+    t0 = time.time()
+    while True:
+        st, tau, cnt, stats = srv.poll(ticket, wait_ms=50)
+        if st == nlos.OK:
+            return tau, cnt, stats
+        assert time.time() - t0 < timeout_s, "request did not finish"
+
+
+def test_served_in_a_mix_equals_alone():
+    from paper_2506_03747_gb300 import nlos
+    H.lib()
+    reqs = _requests(14)
+    srv = nlos.server_create(8 << 30)
+    tickets = [srv.submit(p, pts) for p, pts in reqs]
+    for (prm, pts), t in zip(reqs, tickets):
+        tau_ptr, cnt_ptr, stats = _wait(srv, t)
+        S = prm["scan_nx"] * prm["scan_ny"]
+        B = prm["num_bins"]
+        tau = _fetch(tau_ptr, (S, B), torch.float32)
+        a_tau, a_cnt, a_st = _alone(prm, pts)
+        H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=1e-5,
+                     what=f"served vs alone ({prm['scan_nx']}x{prm['scan_ny']}x{B})")
+        if a_cnt is not None:
+            cnt = _fetch(cnt_ptr, (S, B), torch.int32).view(np.uint32)
+            diff = int((cnt != a_cnt).sum())
+            assert diff <= max(2, cnt.size // 10000), diff
+            assert stats["noise_scale"] == pytest.approx(a_st["noise_scale"], rel=1e-5)
+        assert stats["pairs"] == S * pts.shape[0]
+        srv.release(t)
+    srv.destroy()
+
+
+def test_admission_respects_budget_and_all_finish():
+    from paper_2506_03747_gb300 import nlos
+    H.lib()
+    reqs = _requests(10, seed=5)
+    # budget of about two requests at a time
+    budget = 24 << 20
+    srv = nlos.server_create(budget)
+    tickets = [srv.submit(p, pts) for p, pts in reqs]
+    done = set()
+    peak = 0
+    t0 = time.time()
+    while len(done) < len(tickets):
+        peak = max(peak, srv.stats()["resident_bytes"])
+        for t in tickets:
+            if t in done:
+                continue
+            st, _, _, _ = srv.poll(t, wait_ms=0)
+            if st == nlos.OK:
+                done.add(t)
+                srv.release(t)
+            elif st != nlos.EBUSY:
+                raise AssertionError(f"request failed with {st}")
+        assert time.time() - t0 < 120
+        time.sleep(0.001)
+    assert 0 < peak <= budget
+    srv.destroy()
+
+
+def test_oversized_request_and_cancellation_and_refused_allocation():
+    from paper_2506_03747_gb300 import nlos
+    H.lib()
+    reqs = _requests(4, seed=9)
+    srv = nlos.server_create(1 << 20)  # 1 MiB: every request here is larger
+    t = srv.submit(*reqs[0])
+    with pytest.raises(nlos.NlosError) as ei:
+        _wait(srv, t, 10)
+    assert ei.value.status == nlos.ENOMEM
+    srv.release(t)
+    srv.destroy()
+
+    srv = nlos.server_create(8 << 30)
+    srv.inject(2)  # next admission: allocation refused
+    t = srv.submit(*reqs[1])
+    with pytest.raises(nlos.NlosError) as ei:
+        _wait(srv, t, 10)
+    assert ei.value.status == nlos.ENOMEM
+    srv.release(t)
+    # cancellation of a request that is still queued: a burst, cancel the last
+    ts = [srv.submit(*reqs[i % 4]) for i in range(8)]
+    srv.release(ts[-1])
+    with pytest.raises(nlos.NlosError) as ei:
+        srv.poll(ts[-1])
+    assert ei.value.status in (nlos.ENOTFOUND,)
+    for t in ts[:-1]:
+        _wait(srv, t)
+        srv.release(t)
+    srv.destroy()
+
+
+def test_withheld_publication_times_out_and_server_recovers():
+    from paper_2506_03747_gb300 import nlos
+    H.lib()
+    reqs = _requests(3, seed=13)
+    srv = nlos.server_create(8 << 30)
+    srv.inject(1)  # the next request's first work item is never published
+    t = srv.submit(*reqs[0])
+    with pytest.raises(nlos.NlosError) as ei:
+        _wait(srv, t, 30)
+    assert ei.value.status == nlos.ETIMEOUT
+    srv.release(t)
+    # the server keeps serving
+    t2 = srv.submit(*reqs[1])
+    tau_ptr, _, stats = _wait(srv, t2, 30)
+    prm, pts = reqs[1]
+    S, B = prm["scan_nx"] * prm["scan_ny"], prm["num_bins"]
+    tau = _fetch(tau_ptr, (S, B), torch.float32)
+    a_tau, _, _ = _alone(prm, pts)
+    H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=1e-5, what="after fault")
+    srv.release(t2)
+    srv.destroy()
