@@ -273,10 +273,10 @@ static float stream_uniform(orc_stream* st) {
  * Poisson sampling (Eq. 18/19). The sampled count decides an integer, so the
  * host and the device take each decision in the same precision: lambda is a
  * single-precision value and the uniforms are exact in single precision;
- *  - lambda < 10: Knuth's multiplication method in single precision (multiply
+ *  - lambda < 30: Knuth's multiplication method in single precision (multiply
  *    uniforms until the product drops to expf(-lambda) or below; the count is
  *    the number of factors minus one);
- *  - lambda >= 10: PTRS, the transformed rejection method with squeeze of
+ *  - lambda >= 30: PTRS, the transformed rejection method with squeeze of
  *    W. Hoermann, "The transformed rejection method for generating Poisson
  *    random variables", Insurance: Mathematics and Economics 12 (1993),
  *    evaluated in double (log and lgamma of double agree to about the last
@@ -322,7 +322,7 @@ uint32_t orc_poisson_one(float lam, uint64_t index, uint64_t seed, uint32_t stre
   if (!(lam > 0.0f)) return 0u;
   orc_stream st;
   stream_init(&st, index, seed, stream_tag);
-  return lam < 10.0f ? poisson_knuth(lam, &st) : poisson_ptrs(lam, &st);
+  return lam < 30.0f ? poisson_knuth(lam, &st) : poisson_ptrs(lam, &st);
 }
 
 void orc_poisson(const float* lam, int64_t n, uint64_t index_base, uint64_t seed,

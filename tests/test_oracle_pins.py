@@ -370,10 +370,10 @@ def test_philox_avalanche():
 
 # ---------------------------------------------------------------------------
 # Poisson sampler (Eq. 18/19): mean, variance and the full pmf (chi-square)
-# against the Poisson distribution, for the Knuth (lambda < 10) and PTRS
-# (lambda >= 10) branches.
+# against the Poisson distribution, for the Knuth (lambda < 30) and PTRS
+# (lambda >= 30) branches.
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("lam", [1e-3, 0.5, 3.0, 9.9, 10.0, 27.5, 100.0, 1500.0])
+@pytest.mark.parametrize("lam", [1e-3, 0.5, 3.0, 9.9, 27.5, 29.9, 30.0, 100.0, 1500.0])
 def test_poisson_sampler_distribution(lam):
     stats = pytest.importorskip("scipy.stats")
     n = 200_000
