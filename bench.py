@@ -292,12 +292,113 @@ def run_ours(args):
             "roofline": roof, "e2e": e2e}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(params, pts_np, args.cpu_scan)
+    if rank == 0 and ws == 1 and args.serving_requests > 0:
+        line["serving"] = serving_bench(args.serving_requests, args.serving_rate)
     if rank == 0:
         print(json.dumps(line), flush=True)
     scene.destroy()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
+    """Replays one seeded Poisson-arrival trace (the serving workload: scan side
+    16-256, bins 256-2048, 4-16 ps, 1e4-2e6 points, confocal or not, union or
+    heightfield scene) through (i) the continuous-batching server and (ii) one
+    request at a time (scene create + simulate + wait + destroy, in arrival
+    order). Latency = result ready on the device (observed by the host) minus
+    arrival."""
+    import threading
+    import torch
+    import scenes
+    from paper_2506_03747_gb300 import nlos
+
+    reqs = scenes.serving_trace(n_requests=n_requests, rate_hz=rate_hz)
+    # point pools: one union scene and one heightfield of ~2M points; a request
+    # with P points takes P pool points (patch areas rescaled by pool/P)
+    rng = np.random.default_rng(scenes.SEED_BASE + 55)
+    pool_u, _ = scenes.primitive_union_points(rng, 2_000_000)
+    pool_h = scenes.heightfield_points(rng, 1415)
+    pool_u = pool_u[rng.permutation(len(pool_u))]
+    pool_h = pool_h[rng.permutation(len(pool_h))]
+    pts_of = []
+    for r in reqs:
+        pool = pool_u if r["kind"] == "union" else pool_h
+        P = min(r["n_points"], len(pool))
+        p = pool[:P].copy()
+        p[:, 7] *= len(pool) / P
+        pts_of.append(p)
+    pairs = [r["params"]["scan_nx"] * r["params"]["scan_ny"] * len(p) for r, p in zip(reqs, pts_of)]
+
+    # (i) continuous batching
+    srv = nlos.server_create(int(budget_gb * (1 << 30)))
+    t0 = time.perf_counter() + 0.05
+    tickets = [None] * len(reqs)
+    done_at = [None] * len(reqs)
+    failures = []
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            dt = t0 + r["arrival_s"] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(r["params"], pts_of[i])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    pending = set(range(len(reqs)))
+    while pending:
+        for i in list(pending):
+            if tickets[i] is None:
+                continue
+            try:
+                st, _, _, _ = srv.poll(tickets[i], wait_ms=0)
+            except nlos.NlosError as e:  # a failed request counts as done, reported
+                failures.append((i, str(e)))
+                st = nlos.OK
+            if st == nlos.OK:
+                done_at[i] = time.perf_counter()
+                srv.release(tickets[i])
+                pending.discard(i)
+        time.sleep(0.0002)
+    th.join()
+    srv.destroy()
+    lat_b = np.array([done_at[i] - (t0 + reqs[i]["arrival_s"]) for i in range(len(reqs))])
+    span_b = max(done_at) - t0
+
+    # (ii) one request at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter() + 0.05
+    done1 = []
+    for i, r in enumerate(reqs):
+        dt = t0 + r["arrival_s"] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        prm = nlos.params(r["params"])
+        sc = nlos.scene_create(prm, pts_of[i])
+        S, B = sc.num_scan, sc.num_bins
+        tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+        cnt = torch.empty((S, B), dtype=torch.int32, device="cuda")
+        nlos.simulate(sc, tau, cnt, None)
+        torch.cuda.synchronize()
+        done1.append(time.perf_counter())
+        sc.destroy()
+        del tau, cnt
+    lat_1 = np.array([done1[i] - (t0 + reqs[i]["arrival_s"]) for i in range(len(reqs))])
+    span_1 = max(done1) - t0
+    tot_pairs = float(sum(pairs))
+
+    def summ(lat, span):
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3),
+                "req_per_s": len(lat) / span, "pairs_per_s": tot_pairs / span}
+
+    return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "budget_gb": budget_gb,
+            "offered_pairs_per_s": tot_pairs / reqs[-1]["arrival_s"],
+            "continuous_batching": summ(lat_b, span_b), "one_at_a_time": summ(lat_1, span_1),
+            "failures": failures[:5]}
 
 
 def main():
@@ -310,6 +411,10 @@ def main():
                     help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--cpu-scan", type=int, default=2048,
                     help="scan points in the CPU baseline sample")
+    ap.add_argument("--serving-requests", type=int, default=200,
+                    help="requests in the serving replay (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=200.0,
+                    help="Poisson arrival rate of the serving replay [1/s]")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -212,7 +212,7 @@ nlos_status nlos_reduce(const float* tau_dev, uint64_t num_traces, uint32_t num_
  * the Philox4x32-10 stream of global bin index index_base + i: key =
  * (seed_lo, seed_hi), counter = (index_lo, index_hi, block, stream_tag),
  * uniforms ((word >> 9) + 0.5) * 2^-23; Knuth's multiplication method for
- * lambda < 10, Hoermann's PTRS (1993) otherwise, in single precision. */
+ * lambda < 30 (single precision), Hoermann's PTRS (1993) otherwise (double). */
 nlos_status nlos_noise(const float* tau_dev, uint64_t n, float scale, float dark, uint64_t seed,
                        uint32_t stream_tag, uint64_t index_base, uint32_t* counts_dev,
                        void* cuda_stream);

@@ -16,10 +16,15 @@ namespace nlos {
 // keep the compiler from contracting into FMAs).
 // Per-bin stream: key = (seed_lo, seed_hi), counter = (index_lo, index_hi,
 // block, stream_tag); a word w gives the uniform ((w >> 9) + 0.5) * 2^-23.
-//  * lambda < 10: Knuth's multiplication method against expf(-lambda);
-//  * lambda >= 10: Hoermann's PTRS (1993), transformed rejection with squeeze,
+//  * lambda < 30: Knuth's multiplication method against expf(-lambda);
+//  * lambda >= 30: Hoermann's PTRS (1993), transformed rejection with squeeze,
 //    in double.
 // ---------------------------------------------------------------------------
+// Both samplers are exact; the switch point only moves work between Knuth's
+// single-precision products and the PTRS branch, which runs in FP64 (slow on
+// this part), so it sits where PTRS becomes cheaper than ~lambda products.
+constexpr float kKnuthMax = 30.0f;
+
 struct BinStream {
   uint4 ctr;
   uint32_t k0, k1;
@@ -85,7 +90,7 @@ __device__ __forceinline__ uint32_t poisson_sample(float lam, uint64_t index, ui
                                                    uint32_t tag) {
   if (!(lam > 0.0f)) return 0u;
   BinStream st(index, seed, tag);
-  return lam < 10.0f ? poisson_knuth(lam, st) : poisson_ptrs(lam, st);
+  return lam < kKnuthMax ? poisson_knuth(lam, st) : poisson_ptrs(lam, st);
 }
 
 

@@ -233,8 +233,9 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         const long long t1 = clock64();
         while (ld_acquire_sys(&slot->seq) != got) {
           if (clock64() - t1 > kWaitCycles) {
+            *reinterpret_cast<volatile uint64_t*>(&q.ctl->err_item) = got;
+            __threadfence_system();
             atomicOr_system(&q.ctl->err, kErrWaitTimeout);
-            atomicExch(reinterpret_cast<unsigned long long*>(&q.ctl->err_item), got);
             got = kSkip;
             break;
           }
@@ -342,10 +343,11 @@ struct Server {
   uint64_t next_ticket = 1;
   int device = 0, num_sms = 0;
   cudaStream_t kstream = nullptr, cstream = nullptr;
-  Control* ctl = nullptr;
+  Control* ctl = nullptr;       // host addresses of the mapped structures
   WorkItem* ring = nullptr;
   JobDesc* jobs = nullptr;
   JobStatus* status = nullptr;
+  ServeArgs dev_args{};         // device addresses of the same memory
   unsigned long long* d_head = nullptr;
   uint64_t published = 0;
   bool kernel_running = false;
@@ -659,7 +661,7 @@ bool step(Server& sv) {
   if (sv.kernel_running && cudaEventQuery(sv.kernel_done) == cudaSuccess) sv.kernel_running = false;
   if (sv.published > completed && !sv.kernel_running) {
     __atomic_store_n(&sv.ctl->park, 0u, __ATOMIC_RELEASE);
-    ServeArgs q{sv.ctl, sv.ring, sv.jobs, sv.status, sv.d_head};
+    ServeArgs q = sv.dev_args;
     serve_kernel<<<sv.num_sms, kServeThreads, sv.smem, sv.kstream>>>(q);
     cudaEventRecord(sv.kernel_done, sv.kstream);
     sv.kernel_running = true;
@@ -727,6 +729,12 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
   std::memset(sv.jobs, 0, sizeof(JobDesc) * kMaxJobs);
   std::memset(sv.status, 0, sizeof(JobStatus) * kMaxJobs);
   if ((e = cudaMalloc(&sv.d_head, sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.ctl), sv.ctl, 0)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.ring), sv.ring, 0)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.jobs), sv.jobs, 0)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.status), sv.status, 0)) != cudaSuccess)
+    return fail(e, "cudaHostGetDevicePointer");
+  sv.dev_args.head = sv.d_head;
   if ((e = cudaMemset(sv.d_head, 0, sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMemset");
   if ((e = cudaStreamCreateWithFlags(&sv.kstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
   if ((e = cudaStreamCreateWithFlags(&sv.cstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");

@@ -58,11 +58,11 @@ def _alone(prm, pts):
 
 
 class _DevView:
-    """A read-only view of server-owned device memory (CUDA array interface)."""
+    """A view of server-owned device memory (CUDA array interface), copied at once."""
 
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3}
+                                         "data": (int(ptr), False), "version": 3}
 
 
 def _fetch(ptr, shape, dtype):
