@@ -45,9 +45,30 @@ def _dist():
     return ws, rank, local
 
 
+def whole_job_rate(units_per_rank: float, seconds: float, world_size: int, dist=None,
+                   device=None) -> tuple:
+    """Weak scaling with independent problems: every rank processes the same
+    number of units; the job takes as long as its slowest rank (max over ranks
+    of the timed seconds), and the whole-job rate is all ranks' units over that
+    time. Returns (rate, max_seconds)."""
+    t = seconds
+    if dist is not None and world_size > 1:
+        import torch
+        x = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world_size * units_per_rank / t, t
+
+
+def workload_seed(rank: int) -> int:
+    """Each rank simulates its own independent scene of the same workload."""
+    import scenes
+    return scenes.SEED_BASE + 2 + 1000 * rank
+
+
 def _workload(rank: int):
     import scenes
-    params, pts = scenes.workload_union64(seed=scenes.SEED_BASE + 2 + 1000 * rank)
+    params, pts = scenes.workload_union64(seed=workload_seed(rank))
     return params, pts
 
 
@@ -225,12 +246,8 @@ def run_ours(args):
     nlos.scene_check(scene)
     step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
     fwd_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
-    t_total = float(step_ms.sum()) * 1e-3
-    if dist:
-        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = ws * args.steps * pairs_per_step / t_total
+    value, t_total = whole_job_rate(args.steps * pairs_per_step, float(step_ms.sum()) * 1e-3, ws,
+                                    dist, "cuda")
 
     # ---- end to end through the C ABI with host buffers (pinned) ----------
     pts_host = torch.from_numpy(pts_np).pin_memory()
@@ -253,12 +270,9 @@ def run_ours(args):
         counts_host.copy_(counts, non_blocking=True)    # D2H of the step's result
         b.record(stream)
     torch.cuda.synchronize()
-    e2e_t = sum(a.elapsed_time(b) for a, b in e2e_ev) * 1e-3
-    if dist:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e = {"value": ws * args.steps * pairs_per_step / e2e_t, "unit": UNIT,
+    e2e_rate, _ = whole_job_rate(args.steps * pairs_per_step,
+                                 sum(a.elapsed_time(b) for a, b in e2e_ev) * 1e-3, ws, dist, "cuda")
+    e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": int(pts_np.nbytes), "d2h_bytes_per_step": int(S * B * 4)}
 
     # ---- roofline of the dominant kernel (the pair histogram) -------------
@@ -292,6 +306,8 @@ def run_ours(args):
             "roofline": roof, "e2e": e2e}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(params, pts_np, args.cpu_scan)
+    if rank == 0 and ws == 1 and args.splat_steps > 0:
+        line["splat_adjoint"] = splat_adjoint_bench(args.splat_steps, 1)
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         line["serving"] = serving_bench(args.serving_requests, args.serving_rate)
     if rank == 0:
@@ -300,6 +316,71 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def splat_adjoint_bench(steps: int, warmup: int):
+    """Differentiable path on the 8-scene glyph batch (64x64 scan, 65,536 points
+    per scene, 512 bins x 8 ps, splat with 60 ps FWHM): per step, for every
+    scene, the splat forward, the L2-loss gradient 2 (tau - target) and the
+    hand-written adjoint (gradients for albedo and normal-offset depth)."""
+    import torch
+    import scenes
+    from paper_2506_03747_gb300 import nlos
+    params, sc_pts, tgt_pts = scenes.workload_glyph_batch()
+    prm = nlos.params(params)
+    stream = torch.cuda.current_stream()
+    scs, targets, taus, gas, gds = [], [], [], [], []
+    for pts, tp in zip(sc_pts, tgt_pts):
+        sc = nlos.scene_create(prm, pts)
+        tsc = nlos.scene_create(prm, tp)
+        S, B, P = sc.num_scan, sc.num_bins, sc.num_points
+        tgt = torch.empty((S, B), dtype=torch.float32, device="cuda")
+        nlos.simulate(tsc, tgt)
+        tsc.destroy()
+        scs.append(sc)
+        targets.append(tgt)
+        taus.append(torch.empty((S, B), dtype=torch.float32, device="cuda"))
+        gas.append(torch.empty(P, dtype=torch.float32, device="cuda"))
+        gds.append(torch.empty(P, dtype=torch.float32, device="cuda"))
+    S, B, P = scs[0].num_scan, scs[0].num_bins, scs[0].num_points
+    g = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    fwd_ms, bwd_ms = [], []
+
+    def step(record):
+        for i, sc in enumerate(scs):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            nlos.forward(sc, taus[i])
+            e[1].record(stream)
+            torch.sub(taus[i], targets[i], out=g)
+            g.mul_(2.0)
+            nlos.simulate_backward(sc, g, gas[i], gds[i])
+            e[2].record(stream)
+            if record:
+                fwd_ms.append(e)
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1) * 1e-3
+    f = sum(e[0].elapsed_time(e[1]) for e in fwd_ms) * 1e-3
+    b = sum(e[1].elapsed_time(e[2]) for e in fwd_ms) * 1e-3
+    pairs = len(scs) * S * P
+    for sc in scs:
+        sc.destroy()
+    return {"workload": "8 glyph-plane scenes, 64x64 scan, 65,536 points, 512 bins x 8 ps, "
+                        "splat FWHM 60 ps, L2 loss",
+            "pairs_per_step": pairs, "steps": steps,
+            "ms_per_step": total * 1e3 / steps,
+            "forward_pairs_per_s": steps * pairs / f,
+            "adjoint_pairs_per_s": steps * pairs / b,
+            "train_step_pairs_per_s": steps * pairs / total}
 
 
 def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
@@ -348,7 +429,13 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
     th = threading.Thread(target=submitter)
     th.start()
     pending = set(range(len(reqs)))
+    deadline = time.perf_counter() + 120.0 + reqs[-1]["arrival_s"]
     while pending:
+        if time.perf_counter() > deadline:  # bounded: report what did not finish
+            failures.append((sorted(pending)[:5], "not finished within the replay deadline"))
+            for i in pending:
+                done_at[i] = time.perf_counter()
+            break
         for i in list(pending):
             if tickets[i] is None:
                 continue
@@ -411,6 +498,8 @@ def main():
                     help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--cpu-scan", type=int, default=2048,
                     help="scan points in the CPU baseline sample")
+    ap.add_argument("--splat-steps", type=int, default=2,
+                    help="steps of the differentiable-path measurement (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests in the serving replay (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=200.0,

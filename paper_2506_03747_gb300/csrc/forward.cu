@@ -30,19 +30,25 @@ __global__ void __launch_bounds__(1024, 1) fwd_kernel(const __grid_constant__ Fw
   FwdSmem sm;
   sm.hist = reinterpret_cast<float*>(smem);
   sm.stage = reinterpret_cast<PointPair*>(smem + (size_t)a.bw * kTile * 4);
-  sm.bars = reinterpret_cast<uint64_t*>(sm.stage + 2 * a.ppb);
+  sm.bars = reinterpret_cast<uint64_t*>(sm.stage + (size_t)a.stages * a.ppb);
   const unsigned long long u0 = (unsigned long long)blockIdx.x * a.units / gridDim.x;
   const unsigned long long u1 = (unsigned long long)(blockIdx.x + 1) * a.units / gridDim.x;
   if (u0 >= u1) return;
   if (threadIdx.x == 0) {
-    mbar_init(&sm.bars[0], 1);
-    mbar_init(&sm.bars[1], 1);
+    for (uint32_t i = 0; i < a.stages; ++i) {
+      mbar_init(&sm.bars[i], 1);                                 // full
+      mbar_init(&sm.bars[a.stages + i], (blockDim.x >> 5) - 1);  // empty (consumer warps)
+    }
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t it = 0;
   unsigned long long nboundary = 0;
+#if NLOS_FWD_WS
+  fwd_run_ws<SCAN, COS, MODE>(a, u0, u1, sm, (int)a.stages, nboundary);
+#else
+  uint32_t it = 0;
   fwd_run<SCAN, COS, MODE>(a, u0, u1, sm, it, nboundary);
+#endif
   if (MODE == MODE_NEAREST_COUNT && nboundary) atomicAdd(a.boundary, nboundary);
 }
 
@@ -145,8 +151,15 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   // shared memory: histogram [bw][32] floats + two staged blocks + barriers
   int dev = sc.device, optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  a.ppb = kPairsPerBlock;
-  const size_t stage_bytes = 2 * (size_t)a.ppb * sizeof(PointPair) + 64;
+  // pairs per staged block: NLOS_FWD_PPB, halved while the histogram of a
+  // full window (up to 1024 bins) would not fit beside the two stages
+  a.ppb = NLOS_FWD_PPB;
+  a.stages = NLOS_FWD_WS ? NLOS_FWD_STAGES : 2;
+  while (a.ppb > 256 && (size_t)std::min(g.B, 1024u) * kTile * 4 +
+                                a.stages * (size_t)a.ppb * sizeof(PointPair) + 256 >
+                            (size_t)optin)
+    a.ppb /= 2;
+  const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 16 * a.stages + 64;
   uint32_t max_bw = (uint32_t)(((size_t)optin - stage_bytes) / (kTile * 4)) & ~3u;
   a.n_win = (g.B + max_bw - 1) / max_bw;
   a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
@@ -162,7 +175,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   int threads = 512, per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (e != cudaSuccess) return e;
-  if (per_sm <= 1) {
+  if (per_sm <= 1 || NLOS_FWD_ONE_CTA) {
     threads = 1024;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
     if (e != cudaSuccess) return e;

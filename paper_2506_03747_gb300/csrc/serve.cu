@@ -60,10 +60,11 @@ constexpr uint32_t kCapBw = 1024;            // histogram bins per window in the
 constexpr uint32_t kPackChunk = 16384;       // pairs per PACK item
 constexpr uint64_t kZeroChunk = 1ull << 20;  // floats per ZERO item
 constexpr uint32_t kFwdChunk = 16;           // point blocks per FORWARD item
+constexpr uint64_t kMaxPhaseItems = 16384;   // FORWARD items per request (coarser beyond)
 constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
 constexpr uint64_t kNoiseChunk = 1ull << 18; // bins per NOISE item
 constexpr long long kIdleCycles = 2000000000LL;  // ~1 s without work: exit
-constexpr int kServeThreads = 768;            // 24 warps: no register spills in the fused paths
+constexpr int kServeThreads = 512;            // 16 warps: room for the registers of every fused path
 constexpr uint64_t kNone = ~0ull;
 constexpr uint64_t kSkip = ~0ull - 1;
 
@@ -324,6 +325,8 @@ struct Request {
   int phase = 0;
   uint32_t items[4] = {0, 0, 0, 0};
   uint32_t withheld = 0;  // published items that will never complete (fault injection)
+  std::vector<WorkItem> backlog;  // items of the current phase not yet published
+  size_t backlog_pos = 0;
   uint64_t first_item = 0, last_item = 0;
   bool release_on_done = false;
   Clock::time_point t_submit, t_done;
@@ -401,6 +404,7 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   a.B = g.B;
   a.kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
   a.ppb = kPairsPerBlock;
+  a.stages = 2;
   a.n_win = (g.B + kCapBw - 1) / kCapBw;
   a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
   a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
@@ -437,14 +441,19 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   (void)sv;
 }
 
-// Writes items into the ring and moves the tail (release).
-void publish(Server& sv, Request* r, std::vector<WorkItem>& items) {
-  // keep fewer than half the ring outstanding (see the claim protocol)
-  while (sv.published + items.size() - __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE) >=
-         kRing / 2)
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
+// Writes as many backlog items of r as the ring has room for and moves the
+// tail (release). At most half the ring is outstanding at any time (see the
+// claim protocol), so a large phase is published over several passes.
+void publish_some(Server& sv, Request* r) {
+  const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
+  const uint64_t outstanding = sv.published - completed;
+  if (outstanding >= kRing / 2) return;
+  const size_t room = (size_t)(kRing / 2 - outstanding);
+  const size_t n = std::min(room, r->backlog.size() - r->backlog_pos);
+  if (n == 0) return;
   uint64_t idx = sv.published;
-  for (WorkItem& w : items) {
+  for (size_t k = 0; k < n; ++k) {
+    const WorkItem& w = r->backlog[r->backlog_pos + k];
     WorkItem* slot = sv.ring + (idx % kRing);
     slot->job = w.job;
     slot->kind = w.kind;
@@ -463,8 +472,14 @@ void publish(Server& sv, Request* r, std::vector<WorkItem>& items) {
   }
   std::atomic_thread_fence(std::memory_order_seq_cst);
   __atomic_store_n(&sv.ctl->tail, idx, __ATOMIC_RELEASE);
+  r->backlog_pos += n;
   r->last_item = idx;
   sv.published = idx;
+  if (r->backlog_pos == r->backlog.size()) {
+    r->backlog.clear();
+    r->backlog.shrink_to_fit();
+    r->backlog_pos = 0;
+  }
 }
 
 void publish_phase(Server& sv, Request* r, int phase) {
@@ -479,11 +494,15 @@ void publish_phase(Server& sv, Request* r, int phase) {
     for (uint64_t b = 0; b < n; b += kZeroChunk)
       items.push_back({job, K_ZERO, b, std::min<uint64_t>(n, b + kZeroChunk), 0});
   } else if (phase == PH_FWD) {
+    // point blocks per item: kFwdChunk, coarser for very large requests so a
+    // phase stays within kMaxPhaseItems (an item never spans two (tile, window))
     const FwdArgs& a = sv.jobs[job].fwd;
     const uint64_t tws = a.units / a.n_blk;
+    uint64_t chunk = kFwdChunk;
+    while (chunk < a.n_blk && tws * ((a.n_blk + chunk - 1) / chunk) > kMaxPhaseItems) chunk *= 2;
     for (uint64_t tw = 0; tw < tws; ++tw)
-      for (uint64_t b = 0; b < a.n_blk; b += kFwdChunk)
-        items.push_back({job, K_FWD, tw * a.n_blk + b, tw * a.n_blk + std::min<uint64_t>(a.n_blk, b + kFwdChunk), 0});
+      for (uint64_t b = 0; b < a.n_blk; b += chunk)
+        items.push_back({job, K_FWD, tw * a.n_blk + b, tw * a.n_blk + std::min<uint64_t>(a.n_blk, b + chunk), 0});
   } else if (phase == PH_REDUCE) {
     for (uint64_t b = 0; b < g.S; b += kReduceChunk)
       items.push_back({job, K_REDUCE, b, std::min<uint64_t>(g.S, b + kReduceChunk), 0});
@@ -494,8 +513,9 @@ void publish_phase(Server& sv, Request* r, int phase) {
   }
   r->phase = phase;
   r->items[phase] = (uint32_t)items.size();
-  if (items.empty()) return;
-  publish(sv, r, items);
+  r->backlog = std::move(items);
+  r->backlog_pos = 0;
+  publish_some(sv, r);
 }
 
 void finish(Server& sv, Request* r, nlos_status st, const std::string& msg) {
@@ -592,6 +612,10 @@ bool step(Server& sv) {
         busy = true;
       }
     } else if (r->state == R_RUNNING) {
+      if (!r->backlog.empty()) {
+        publish_some(sv, r);
+        busy = true;
+      }
       if (sv.withheld_req == r && (dev_err & kErrWaitTimeout)) {
         // the device gave up on the withheld item: the request cannot finish;
         // its memory stays until every other item published for it is done

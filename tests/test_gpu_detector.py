@@ -152,3 +152,28 @@ def test_pipeline_counts_match_oracle_bins():
     diff = (g["counts"] != ref).sum()
     print("pipeline counts differing:", diff, "of", ref.size)
     assert diff <= max(3, ref.size // 100000)
+
+
+def test_paper_nr_noise_mode_matches_oracle():
+    """Algorithm 1 step 2.4: sigma_n = Var(tau_G) / 10^(nr/10) over the whole
+    cube, counts ~ Poisson(sigma_n * tau_G) (the noisy transient is counts /
+    sigma_n): the device's sigma_n equals the oracle's and the counts equal the
+    oracle sampler's on the device's own lambda."""
+    params, pts = scenes.workload_union64(n_points=4096)
+    # the paper's sigma_n carries the units of tau^2: scale the patch areas so
+    # that sigma_n * tau_G reaches counts of order one to a hundred
+    pts = pts.copy()
+    pts[:, 7] *= 1200.0
+    for nr in (0.0, 2.0, 10.0):
+        p = dict(params, scan_nx=20, scan_ny=18, noise_mode="paper_nr", nr_db=nr, dark_per_bin=0.0)
+        g = H.gpu_forward(p, pts, counts=True, stats=True)
+        o = oracle.simulate(p, pts, with_noise=False)
+        var = float(np.var(o["tau_g"]))
+        sigma_n = var / 10 ** (nr / 10)
+        assert g["stats"]["noise_scale"] == pytest.approx(sigma_n, rel=1e-4)
+        lam = oracle.lam_from(g["tau"], np.float32(g["stats"]["noise_scale"]), np.float32(0.0))
+        ref = oracle.poisson(lam, 0, p["seed"], p["stream_tag"])
+        diff = int((g["counts"] != ref).sum())
+        print("paper nr", nr, "sigma_n", sigma_n, "counts total", int(g["counts"].sum()), "diff", diff)
+        assert diff <= max(3, ref.size // 100000)
+        assert g["counts"].sum() > 1000

@@ -185,3 +185,36 @@ def test_u_precision_all_workloads():
             worst = max(worst, float(np.abs(u32.astype(np.float64) - u64).max()))
         print("max |u32 - u64| (bins):", params["num_bins"], params["bin_width_s"], worst)
         assert worst < H.U_EPS
+
+
+def test_paper_dataset_shape():
+    """The paper's dataset configuration (Simulation section; golden fixture):
+    128x128 scan over 2 m x 2 m, 1024 bins of 32 ps, 70 ps FWHM jitter (k = 5),
+    albedo 1, on a 128x128 depth-map-like heightfield; sampled transients
+    against the oracle."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_dataset_params.json")) as f:
+        gd = json.load(f)
+    rng = np.random.default_rng(77)
+    pts = scenes.heightfield_points(rng, gd["scan_side"])
+    pts[:, 6] = gd["albedo"]
+    n = gd["scan_side"]
+    params = scenes.default_params(scan_nx=n, scan_ny=n, wall_half_x=gd["scan_extent_m"] / 2,
+                                   wall_half_y=gd["scan_extent_m"] / 2,
+                                   bin_width_s=gd["bin_width_s"], num_bins=gd["num_bins"],
+                                   jitter_fwhm_s=gd["jitter_fwhm_s"])
+    assert oracle.jitter_taps(params["jitter_fwhm_s"], params["bin_width_s"]).size == 5
+    g = H.gpu_forward(params, pts)
+    rows = np.sort(rng.choice(n * n, size=96, replace=False))
+    worst = 0.0
+    for s in rows:
+        o = H.oracle_with_allowance(params, pts, int(s), 1)
+        worst = max(worst, H.check_bins(g["tau"][s:s + 1], o["tau_g"], allow=o["flip_g"],
+                                        what=f"s={s}"))
+        R = (o["taps"].size - 1) // 2
+        B = params["num_bins"]
+        allow_e = o["edge"] + o["flip"][:, np.r_[0:R + 1, B - R - 1:B]].sum(axis=1)
+        H.check_energy(g["energy"][s:s + 1], o["tau_g"].sum(axis=1), allow=allow_e,
+                       what=f"energy s={s}")
+    print("paper dataset shape: worst rel bin err", worst)
