@@ -208,6 +208,24 @@ nlos_status nlos_jitter(const float* in_dev, float* out_dev, uint64_t num_traces
 nlos_status nlos_reduce(const float* tau_dev, uint64_t num_traces, uint32_t num_bins,
                         double* energy_dev, double* stats_dev, void* cuda_stream);
 
+/* nlos_reduce without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when
+ * they call it (their memory is reserved up front by another allocator, such
+ * as a framework's caching pool, so a new cudaMalloc may fail; or their loop
+ * cannot afford the synchronisation that cudaMalloc/cudaFree may cause).
+ * Same arguments and results as nlos_reduce (energy_dev, stats_dev nullable;
+ * stats_dev receives {double max, double sum, double sumsq}), computed
+ * deterministically (no atomics), asynchronous on cuda_stream.
+ * Limit: num_traces <= 65536 (NLOS_EINVAL beyond). The per-transient partial
+ * results are kept in a fixed 1.5 MiB array in the library's device image,
+ * which every device that loads the library holds until the process exits.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture. Every call reuses the array: calls whose work may overlap on the
+ * GPU (unordered streams) race on it and must be serialised by the caller. */
+nlos_status nlos_reduce_static(const float* tau_dev, uint64_t num_traces, uint32_t num_bins,
+                               double* energy_dev, double* stats_dev, void* cuda_stream);
+
 /* Poisson noise: counts[i] ~ Poisson(fmaf(scale, tau[i], dark)) drawn from
  * the Philox4x32-10 stream of global bin index index_base + i: key =
  * (seed_lo, seed_hi), counter = (index_lo, index_hi, block, stream_tag),

@@ -109,6 +109,7 @@ def load(path: str | None = None):
             "nlos_simulate_backward": (S, [_P, _P, _P, _P, _P]),
             "nlos_jitter": (S, [_P, _P, _U64, _U32, ctypes.c_double, ctypes.c_double, _P]),
             "nlos_reduce": (S, [_P, _U64, _U32, _P, _P, _P]),
+            "nlos_reduce_static": (S, [_P, _U64, _U32, _P, _P, _P]),
             "nlos_noise": (S, [_P, _U64, ctypes.c_float, ctypes.c_float, _U64, _U32, _U64, _P,
                                _P]),
             "nlos_philox": (S, [_P, _U64, _U32, _U32, _P, _P]),
@@ -294,6 +295,13 @@ def jitter(inp, out, num_traces: int, num_bins: int, fwhm_s: float, bin_width_s:
 def reduce(tau, num_traces: int, num_bins: int, energy=None, stats=None, stream=None):
     _check(load().nlos_reduce(_ptr(tau), num_traces, num_bins, _ptr(energy), _ptr(stats),
                               _stream(stream)))
+
+
+def reduce_static(tau, num_traces: int, num_bins: int, energy=None, stats=None, stream=None):
+    """nlos_reduce without device allocation (fixed 1.5 MiB device array,
+    at most 65536 transients per call; overlapping calls race)."""
+    _check(load().nlos_reduce_static(_ptr(tau), num_traces, num_bins, _ptr(energy), _ptr(stats),
+                                     _stream(stream)))
 
 
 def noise(tau, n: int, scale: float, dark: float, seed: int, stream_tag: int, index_base: int,
