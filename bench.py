@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "pair-interactions/s vs FP32 roofline; served p50/p99 latency vs one-by-one"
 UNIT = "pairs/s"
 FP32_SLOTS_PER_PAIR = 17   # algorithmic FP32 issue slots per evaluated pair
+FP32_SLOTS_EARLY_OUT = 6   # slots of a pair stopped by the early out (dx, dy, r^2, cosine)
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 WORKLOAD_DESC = ("union64: confocal 64x64 scan over 2 m x 2 m, 512 bins x 8 ps, stand-off 1 m "
                  "(Euclidean legs), 262,144 area-uniform points on a seeded union of 3-6 "
@@ -125,17 +126,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _traffic_for(kernel_file: str):
+FORWARD_SOURCES = ("forward.cu", "forward_core.cuh", "device_util.cuh", "common.cuh")
+
+
+def forward_sources_sha256() -> str:
+    """One SHA-256 over the sources the forward kernel is compiled from."""
+    h = hashlib.sha256()
+    for name in FORWARD_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_03747_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic_for():
     """DRAM bytes per forward launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "forward_union64_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    with open(kernel_file, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()
-    return d.get("dram_bytes_per_launch") if d.get("forward_cu_sha256") == h else None
+    ok = d.get("forward_sources_sha256") == forward_sources_sha256()
+    return d.get("dram_bytes_per_launch") if ok else None
 
 
 def cpu_baseline(params, pts, scan_count: int):
@@ -281,13 +293,23 @@ def run_ours(args):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_pairs = n_sm * 128 * sm_max * 1e6 / FP32_SLOTS_PER_PAIR
     fwd_mean = float(fwd_ms.mean()) * 1e-3
-    achieved = pairs_per_step / fwd_mean
+    # pairs that went through the full evaluation; the others stopped after
+    # r^2 and the cosine numerator (the warp-uniform early out)
+    st = nlos.simulate(scene, tau, counts, energy, stats=True)
+    full = int(st["pairs_full"])
+    skipped = max(0, pairs_per_step - full)
+    work = full + skipped * FP32_SLOTS_EARLY_OUT / FP32_SLOTS_PER_PAIR
+    achieved = work / fwd_mean
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9,
             "unit": "Gpair/s", "frac": achieved / peak_pairs,
-            "traffic": _traffic_for(os.path.join(ROOT, "paper_2506_03747_gb300", "csrc",
-                                                 "forward.cu")),
+            "traffic": _traffic_for(),
             "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / "
                           f"{FP32_SLOTS_PER_PAIR} FP32 slots per pair",
+            "work_basis": f"full-evaluation-equivalent pairs: pairs evaluated in full + "
+                          f"{FP32_SLOTS_EARLY_OUT}/{FP32_SLOTS_PER_PAIR} x pairs stopped by "
+                          f"the early out",
+            "pairs_full_fraction": full / pairs_per_step,
+            "effective_pairs_per_s": pairs_per_step / fwd_mean,
             "kernel_ms": fwd_mean * 1e3}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -127,6 +127,12 @@ typedef struct {
   double variance;            /* population variance of tau_G (FP64) */
   uint64_t boundary_pairs;    /* pairs with u within boundary_eps of a bin edge */
   uint32_t device_error;      /* nonzero: a bounded device wait gave up */
+  uint64_t pairs_full;        /* pairs that went through the full per-pair
+                                 evaluation, counted per (warp, point pair):
+                                 the forward skips, 32 scan points x 2 surface
+                                 points at a time, pairs that no lane can bin
+                                 (outside the window or facing away), after
+                                 computing only r^2 and the cosine numerator */
 } nlos_stats;
 
 typedef struct nlos_scene nlos_scene;

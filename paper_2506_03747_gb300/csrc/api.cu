@@ -152,10 +152,10 @@ nlos_status nlos_detect(nlos_scene* scene, const float* tau_dev, uint32_t* count
   if (counts_dev && g.noise_mode == NLOS_NOISE_NONE)
     return set_error(NLOS_EINVAL, "counts_dev given but noise_mode is NONE");
   cudaStream_t st = as_stream(cuda_stream);
-  // reset the reduction results (not the forward's boundary count)
+  // reset the reduction results (not the forward's counters)
   NLOS_CUDA_TRY(cudaMemsetAsync(&s.scratch->peak_bits, 0, sizeof(unsigned int), st));
   NLOS_CUDA_TRY(cudaMemsetAsync(&s.scratch->sum, 0,
-                                sizeof(SceneScratch) - offsetof(SceneScratch, sum), st));
+                                offsetof(SceneScratch, pairs_full) - offsetof(SceneScratch, sum), st));
   NLOS_CUDA_TRY(launch_reduce(tau_dev, g.S, g.B, energy_dev, s.scratch, st));
   if (counts_dev)
     NLOS_CUDA_TRY(launch_noise_scene(tau_dev, g.S * (uint64_t)g.B, s.scratch, g.noise_mode,
@@ -198,6 +198,7 @@ nlos_status nlos_simulate(nlos_scene* scene, float* tau_dev, uint32_t* counts_de
     stats->noise_dark = counts_dev ? h.dark : 0.0;
     stats->boundary_pairs = h.boundary_pairs;
     stats->device_error = h.err;
+    stats->pairs_full = h.pairs_full;
     if (h.err & kErrWaitTimeout) return set_error(NLOS_ETIMEOUT, "a bounded device wait gave up");
     if (h.err & kErrBadPoint) return set_error(NLOS_EINVAL, "invalid surface point (see nlos_scene_check)");
   }

@@ -9,13 +9,26 @@
 // with, for x -> x + delta n: dr/d delta = -cos, d cos/d delta = -(1 - cos^2)/r,
 // d(z/r)/d delta = (n_z + (z/r) cos)/r and du/d delta = -(cos_l + cos_d)/(c dt).
 //
-// Schedule: one CTA per (32-scan-point tile, point block); the tile's g rows
-// are staged into shared memory as [bin][32] (lane = scan point, conflict-free
-// gathers); points are broadcast from shared memory; each lane gathers the taps
-// of its own scan point, a warp sum over the 32 scan points gives the tile's
-// contribution to each point, added to the outputs with one global atomic.
+// Two forms of the sums G0, G1:
+//  * taps (any sigma): one CTA per (32-scan-point tile, point block); the
+//    tile's g rows are staged into shared memory as [bin][32] (lane = scan
+//    point, conflict-free gathers) and each lane runs the |x_b| < 6 sigma taps
+//    of its own pair;
+//  * moments (sigma >= 2.5 bins): with u = j + f (j = floor u), c = 1/2 - f
+//    and m = b - j, x_b = m + c, and the Taylor expansion
+//    phi(m + c) = sum_{n < N} D_n[m] c^n (the table of the moment forward)
+//    turns the sums into polynomials in c,
+//      G0 = sum_n c^n H_n[j],                   H_n[j] = sum_m g[j + m] D_n[m],
+//      sigma^2 G1 = sum_n c^n M_n[j] + c G0,    M_n[j] = sum_m g[j + m] m D_n[m],
+//    so a first kernel correlates every transient of g with the 2N tables
+//    (2N floats per (s, j)) and the pair kernel needs one 48-byte gather and
+//    two Horner evaluations per pair instead of about 12 sigma taps.
+// In both, points are broadcast from shared memory, and a warp sum over the
+// 32 scan points of a tile gives the tile's contribution to each point, added
+// to the outputs with one global atomic.
 #include "common.cuh"
 #include "device_util.cuh"
+#include "forward_core.cuh"
 
 #include <cmath>
 
@@ -25,6 +38,8 @@ namespace {
 
 constexpr int kBwdTile = 32;
 constexpr int kBwdPoints = 256;  // points per CTA
+constexpr int kAdjTabThreads = 256;
+static_assert(kMoments == 6, "the adjoint table holds 2 x 6 moments in three float4");
 
 struct BwdArgs {
   const float* raw;        // [P][8]
@@ -67,20 +82,74 @@ __device__ __forceinline__ void leg(int cos_mode, float ndotv, float vz, float n
   dF = (dfc * fw + fc * dfw) * ri2 + fc * fw * 2.0f * c * ri2 * ri;
 }
 
-__global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs a) {
+// H_n[j], M_n[j] of one transient for j = r - J, r in [0, rows), rows = B + 2J,
+// as T[s][r] = {H_0..H_3}, {H_4, H_5, M_0, M_1}, {M_2..M_5}.
+struct AdjTabArgs {
+  const float* g;  // [S][B]
+  float4* T;       // [S][rows][3]
+  uint64_t S;
+  uint32_t B, rows, row_blocks;
+};
+
+__global__ void __launch_bounds__(kAdjTabThreads)
+    adj_table_kernel(const AdjTabArgs a, const __grid_constant__ MomTab mt) {
+  __shared__ float gs[kAdjTabThreads + 2 * kMomMaxJ];
+  const uint64_t s = blockIdx.x / a.row_blocks;
+  const int r0 = (int)(blockIdx.x % a.row_blocks) * kAdjTabThreads;
+  const int J = mt.J;
+  // gs[i] = g[s][r0 - 2J + i] (zero outside the transient)
+  for (int i = threadIdx.x; i < kAdjTabThreads + 2 * J; i += blockDim.x) {
+    const int b = r0 - 2 * J + i;
+    gs[i] = (b >= 0 && b < (int)a.B) ? a.g[s * a.B + b] : 0.0f;
+  }
+  __syncthreads();
+  const int r = r0 + (int)threadIdx.x;
+  if (r >= (int)a.rows) return;
+  float h[kMoments], mm[kMoments];
+#pragma unroll
+  for (int n = 0; n < kMoments; ++n) h[n] = mm[n] = 0.0f;
+  // g[j + m] with j = r - J is gs[threadIdx.x + J + m]
+  const float* gp = gs + threadIdx.x + J;
+  for (int m = -J; m <= J; ++m) {
+    const float gv = gp[m];
+    const float gm = gv * (float)m;
+#pragma unroll
+    for (int n = 0; n < kMoments; ++n) {
+      const float d = mt.d[n][m + J];
+      h[n] = fmaf(gv, d, h[n]);
+      mm[n] = fmaf(gm, d, mm[n]);
+    }
+  }
+  float4* out = a.T + (s * a.rows + (uint64_t)r) * 3;
+  out[0] = make_float4(h[0], h[1], h[2], h[3]);
+  out[1] = make_float4(h[4], h[5], mm[0], mm[1]);
+  out[2] = make_float4(mm[2], mm[3], mm[4], mm[5]);
+}
+
+__device__ __forceinline__ float horner6(float c, float p0, float p1, float p2, float p3, float p4,
+                                         float p5) {
+  return fmaf(fmaf(fmaf(fmaf(fmaf(p5, c, p4), c, p3), c, p2), c, p1), c, p0);
+}
+
+// MOM: T, J and rows of the moment tables (else unused).
+template <bool MOM>
+__global__ void __launch_bounds__(256)
+    bwd_kernel(const BwdArgs a, const float4* __restrict__ T, int J, uint32_t rows) {
   extern __shared__ float sm[];
-  float* gt = sm;                                   // [B][32]
-  float* pts = sm + (size_t)a.B * kBwdTile;         // [kBwdPoints][8]
+  float* gt = sm;                                           // [B][32] (taps form)
+  float* pts = sm + (MOM ? (size_t)0 : (size_t)a.B * kBwdTile);  // [kBwdPoints][8]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const uint64_t n_pblk = (a.P + kBwdPoints - 1) / kBwdPoints;
   const uint64_t tile = blockIdx.x / n_pblk;
   const uint64_t p0 = (blockIdx.x % n_pblk) * kBwdPoints;
   const int np = (int)min((uint64_t)kBwdPoints, a.P - p0);
 
-  for (uint32_t i = tid; i < a.B * kBwdTile; i += blockDim.x) {
-    const uint32_t s_loc = i & 31, b = i >> 5;
-    const uint64_t s = tile * kBwdTile + s_loc;
-    gt[i] = s < a.S ? a.g[s * a.B + b] : 0.0f;
+  if (!MOM) {
+    for (uint32_t i = tid; i < a.B * kBwdTile; i += blockDim.x) {
+      const uint32_t s_loc = i & 31, b = i >> 5;
+      const uint64_t s = tile * kBwdTile + s_loc;
+      gt[i] = s < a.S ? a.g[s * a.B + b] : 0.0f;
+    }
   }
   for (int i = tid; i < np * 8; i += blockDim.x) pts[i] = a.raw[p0 * 8 + i];
   __syncthreads();
@@ -113,20 +182,35 @@ __global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs a) {
     const float u = (rl + rd) * a.inv_cdt + sp.off;
     const float du_dd = -(cl + cd) * a.inv_cdt;
     float G0 = 0.f, G1 = 0.f;
-    if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f)) {
+    if (MOM) {
+      const float fl = floorf(u);
+      if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f) && fl >= (float)-J &&
+          fl < (float)((int)rows - J)) {
+        const float c = 0.5f - (u - fl);
+        const float4* t = T + (s * rows + (uint64_t)((int)fl + J)) * 3;
+        const float4 t0 = __ldg(t), t1 = __ldg(t + 1), t2 = __ldg(t + 2);
+        G0 = horner6(c, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y);
+        const float gm = horner6(c, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w);
+        G1 = fmaf(c, G0, gm) * a.inv_s2;
+      }
+    } else if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f)) {
       const int lo = max(0, (int)(floorf(u - 0.5f - a.reach) + 1.0f));
       const int hi = min((int)a.B - 1, (int)(ceilf(u - 0.5f + a.reach) - 1.0f));
       if (lo <= hi) {
-        float xb = (float)lo + 0.5f - u;
-        float K = a.norm * expf(-xb * xb * a.inv2s2);
-        float r = expf(-(2.0f * xb + 1.0f) * a.inv2s2);
+        // tap recurrence restarted every 8 taps (its rounding error grows
+        // with the square of the number of steps)
+        float K = 0.f, r = 0.f;
         for (int b = lo; b <= hi; ++b) {
+          const float xb = (float)b + 0.5f - u;
+          if (((b - lo) & 7) == 0) {
+            K = a.norm * expf(-xb * xb * a.inv2s2);
+            r = expf(-(2.0f * xb + 1.0f) * a.inv2s2);
+          }
           const float gv = gt[b * kBwdTile + lane];
           G0 = fmaf(gv, K, G0);
           G1 = fmaf(gv * xb, K, G1);
           K *= r;
           r *= a.qstep;
-          xb += 1.0f;
         }
         G1 *= a.inv_s2;
       }
@@ -176,15 +260,40 @@ cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* g
   a.norm = (float)(1.0 / (s * std::sqrt(2.0 * 3.14159265358979323846)));
   a.reach = (float)(6.0 * s);
   a.qstep = (float)std::exp(-1.0 / (s * s));
+  const uint64_t blocks = ((g.P + kBwdPoints - 1) / kBwdPoints) * ((g.S + kBwdTile - 1) / kBwdTile);
+  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+  if (use_moments(s)) {
+    // moment tables: S x (B + 2J) x 48 bytes, stream-ordered, freed after use
+    MomTab mt;
+    moment_table(s, mt);
+    AdjTabArgs t{};
+    t.g = grad_tau;
+    t.S = g.S;
+    t.B = g.B;
+    t.rows = g.B + 2u * (uint32_t)mt.J;
+    t.row_blocks = (t.rows + kAdjTabThreads - 1) / kAdjTabThreads;
+    const uint64_t tab_blocks = g.S * t.row_blocks;
+    if (tab_blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&t.T), sizeof(float4) * 3 * g.S * t.rows, st);
+    if (e != cudaSuccess) return e;
+    adj_table_kernel<<<(unsigned)tab_blocks, kAdjTabThreads, 0, st>>>(t, mt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      const size_t smem = sizeof(float) * kBwdPoints * 8;
+      bwd_kernel<true><<<(unsigned)blocks, 256, smem, st>>>(a, t.T, mt.J, t.rows);
+      e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(t.T, st);
+    return e != cudaSuccess ? e : ef;
+  }
   const size_t smem = sizeof(float) * ((size_t)g.B * kBwdTile + kBwdPoints * 8);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sc.device);
   if (smem > (size_t)optin) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
-  const uint64_t blocks = ((g.P + kBwdPoints - 1) / kBwdPoints) * ((g.S + kBwdTile - 1) / kBwdTile);
-  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-  bwd_kernel<<<(unsigned)blocks, 256, smem, st>>>(a);
+  bwd_kernel<false><<<(unsigned)blocks, 256, smem, st>>>(a, nullptr, 0, 0);
   return cudaGetLastError();
 }
 

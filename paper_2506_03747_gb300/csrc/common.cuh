@@ -65,9 +65,11 @@ struct SceneScratch {
   double sumsq;               // FP64 sum of squares
   float scale;                // noise scale (computed on the device)
   float dark;
+  unsigned long long pairs_full;  // pairs through the full evaluation (past the early out)
+  unsigned long long pad3;
 };
 constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
-static_assert(sizeof(SceneScratch) == 48, "scratch layout");
+static_assert(sizeof(SceneScratch) == 64, "scratch layout");
 
 struct Geometry {
   // host-side resolved parameters

@@ -25,11 +25,14 @@ namespace nlos {
 
 // Standalone launch: the units of one job split evenly over a persistent grid.
 template <int SCAN, int COS, int MODE>
-__global__ void __launch_bounds__(1024, 1) fwd_kernel(const __grid_constant__ FwdArgs a) {
+__global__ void __launch_bounds__(1024, 1)
+    fwd_kernel(const __grid_constant__ FwdArgs a, const __grid_constant__ MomTab mt) {
   extern __shared__ __align__(128) unsigned char smem[];
   FwdSmem sm;
+  const size_t hist_bytes = (MODE == MODE_SPLAT_MOM) ? (size_t)kMoments * kMomRows * kTile * 4
+                                                     : (size_t)a.bw * kTile * 4;
   sm.hist = reinterpret_cast<float*>(smem);
-  sm.stage = reinterpret_cast<PointPair*>(smem + (size_t)a.bw * kTile * 4);
+  sm.stage = reinterpret_cast<PointPair*>(smem + hist_bytes);
   sm.bars = reinterpret_cast<uint64_t*>(sm.stage + (size_t)a.stages * a.ppb);
   const unsigned long long u0 = (unsigned long long)blockIdx.x * a.units / gridDim.x;
   const unsigned long long u1 = (unsigned long long)(blockIdx.x + 1) * a.units / gridDim.x;
@@ -42,14 +45,20 @@ __global__ void __launch_bounds__(1024, 1) fwd_kernel(const __grid_constant__ Fw
     fence_mbar_init();
   }
   __syncthreads();
-  unsigned long long nboundary = 0;
+  FwdCount cnt;
 #if NLOS_FWD_WS
-  fwd_run_ws<SCAN, COS, MODE>(a, u0, u1, sm, (int)a.stages, nboundary);
+  fwd_run_ws<SCAN, COS, MODE>(a, u0, u1, sm, (int)a.stages, cnt, &mt);
 #else
-  uint32_t it = 0;
-  fwd_run<SCAN, COS, MODE>(a, u0, u1, sm, it, nboundary);
+  if (MODE == MODE_SPLAT_MOM) {
+    fwd_run_ws<SCAN, COS, MODE>(a, u0, u1, sm, (int)a.stages, cnt, &mt);
+  } else {
+    uint32_t it = 0;
+    fwd_run<SCAN, COS, MODE>(a, u0, u1, sm, it, cnt);
+  }
 #endif
-  if (MODE == MODE_NEAREST_COUNT && nboundary) atomicAdd(a.boundary, nboundary);
+  if (MODE == MODE_NEAREST_COUNT && cnt.boundary) atomicAdd(a.boundary, cnt.boundary);
+  // the count is warp-uniform: one lane adds it, 64 pairs per warp iteration
+  if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
 }
 
 // Per-pair table (debug/parity): the same pair_eval2 on pair k for scan point
@@ -67,7 +76,6 @@ __global__ void pair_table_kernel(const PointPair* pairs, uint32_t n_pairs, uint
   load_pair(pairs + k, q);
   float2 u, w, cn;
   pair_eval2<SCAN, COS>(q, make_float2(-sp.sx, -sp.sx), make_float2(-sp.sy, -sp.sy),
-                        make_float2(sp.sx, sp.sx), make_float2(sp.sy, sp.sy),
                         make_float2(sp.off, sp.off), make_float2(kbin, kbin), u, w, cn);
   if (!facing<COS>(cn.x)) w.x = 0.f;
   if (!facing<COS>(cn.y)) w.y = 0.f;
@@ -87,13 +95,14 @@ __global__ void pair_table_kernel(const PointPair* pairs, uint32_t n_pairs, uint
 // ---------------------------------------------------------------------------
 namespace {
 
-using FwdFn = void (*)(FwdArgs);
+using FwdFn = void (*)(FwdArgs, MomTab);
 
 template <int SCAN, int COS>
 FwdFn pick_mode(int mode) {
   switch (mode) {
     case MODE_NEAREST: return fwd_kernel<SCAN, COS, MODE_NEAREST>;
     case MODE_NEAREST_COUNT: return fwd_kernel<SCAN, COS, MODE_NEAREST_COUNT>;
+    case MODE_SPLAT_MOM: return fwd_kernel<SCAN, COS, MODE_SPLAT_MOM>;
     default: return fwd_kernel<SCAN, COS, MODE_SPLAT>;
   }
 }
@@ -111,6 +120,27 @@ FwdFn pick(int scan, int cos, int mode) {
 
 }  // namespace
 
+// D_n[j] = K^(n)(j) / n! for the Gaussian K(x) = exp(-x^2/(2 s^2)) / (s sqrt(2 pi)):
+// K^(n)(x) = (-1)^n He_n(x/s) K(x) / s^n with the probabilists' Hermite
+// polynomials He_0 = 1, He_1 = t, He_{n+1} = t He_n - n He_{n-1} (FP64).
+void moment_table(double s, MomTab& mt) {
+  mt.J = (int)std::ceil(6.0 * s) + 1;
+  for (int j = -mt.J; j <= mt.J; ++j) {
+    const double t = (double)j / s;
+    const double k = std::exp(-0.5 * t * t) / (s * std::sqrt(2.0 * 3.14159265358979323846));
+    double he[kMoments];
+    he[0] = 1.0;
+    if (kMoments > 1) he[1] = t;
+    for (int n = 1; n + 1 < kMoments; ++n) he[n + 1] = t * he[n] - n * he[n - 1];
+    double fact = 1.0, spow = 1.0;
+    for (int n = 0; n < kMoments; ++n) {
+      if (n >= 1) fact *= n;
+      mt.d[n][j + mt.J] = (float)(((n & 1) ? -1.0 : 1.0) * he[n] * k / (spow * fact));
+      spow *= s;
+    }
+  }
+}
+
 int jitter_radius(double sigma) {
   if (!(sigma > 0.0)) return 0;
   return (int)std::ceil(2.0 * sigma);
@@ -127,13 +157,18 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   a.tau = tau;
   a.err = &sc.scratch->err;
   a.boundary = &sc.scratch->boundary_pairs;
+  a.pairs_full = &sc.scratch->pairs_full;
   a.n_pairs = (uint32_t)((g.P + 1) / 2);
   a.S = (uint32_t)g.S;
   a.B = g.B;
   a.kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
   const bool splat = g.bin_mode == NLOS_BIN_SPLAT;
-  const int mode = splat ? MODE_SPLAT
-                         : (sc.params.boundary_eps > 0.f ? MODE_NEAREST_COUNT : MODE_NEAREST);
+  MomTab mt{};
+  const bool moments = splat && use_moments(g.sigma);
+  const int mode = moments ? MODE_SPLAT_MOM
+                   : splat ? MODE_SPLAT
+                           : (sc.params.boundary_eps > 0.f ? MODE_NEAREST_COUNT : MODE_NEAREST);
+  if (moments) moment_table(g.sigma, mt);
   a.eps = sc.params.boundary_eps;
   if (splat) {
     const double s = g.sigma;
@@ -159,11 +194,28 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
                                 a.stages * (size_t)a.ppb * sizeof(PointPair) + 256 >
                             (size_t)optin)
     a.ppb /= 2;
+  if (moments) {
+    a.ppb = kPairsPerBlock;
+    a.stages = 2;
+  }
   const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 16 * a.stages + 64;
-  uint32_t max_bw = (uint32_t)(((size_t)optin - stage_bytes) / (kTile * 4)) & ~3u;
-  a.n_win = (g.B + max_bw - 1) / max_bw;
-  a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
-  const size_t smem = (size_t)a.bw * kTile * 4 + stage_bytes;
+  size_t smem;
+  if (moments) {
+    // window rows plus 2J halo rows fit the kMomRows moment histograms
+    const uint32_t max_bw = (uint32_t)(kMomRows - 2 * mt.J) & ~3u;
+    a.n_win = (g.B + max_bw - 1) / max_bw;
+    a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
+    if (a.bw > max_bw) {
+      a.bw = max_bw;
+      a.n_win = (g.B + a.bw - 1) / a.bw;
+    }
+    smem = (size_t)kMoments * kMomRows * kTile * 4 + stage_bytes;
+  } else {
+    uint32_t max_bw = (uint32_t)(((size_t)optin - stage_bytes) / (kTile * 4)) & ~3u;
+    a.n_win = (g.B + max_bw - 1) / max_bw;
+    a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
+    smem = (size_t)a.bw * kTile * 4 + stage_bytes;
+  }
   const uint32_t n_tiles = (uint32_t)((g.S + kTile - 1) / kTile);
   a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
   a.units = (unsigned long long)n_tiles * a.n_win * a.n_blk;
@@ -183,7 +235,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   unsigned long long grid = (unsigned long long)sc.num_sms * per_sm;
   if (grid > a.units) grid = a.units;
-  fn<<<(unsigned)grid, threads, smem, st>>>(a);
+  fn<<<(unsigned)grid, threads, smem, st>>>(a, mt);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,8 @@
 #include "common.cuh"
 #include "device_util.cuh"
 
+#include <cmath>
+
 namespace nlos {
 
 constexpr int kTile = 32;                   // scan points per CTA tile
@@ -32,19 +34,60 @@ constexpr int kMagicBits = 0x4B400000;      // bit pattern of kMagic
 constexpr int kMaxTaps = 129;               // fused jitter: R <= 64
 constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged block
 #ifndef NLOS_FWD_PPB
-#define NLOS_FWD_PPB 256                    // standalone forward: pairs per staged block
+#define NLOS_FWD_PPB 512                    // standalone forward: pairs per staged block
 #endif
 #ifndef NLOS_FWD_ONE_CTA
-#define NLOS_FWD_ONE_CTA 0                  // standalone forward: 1 CTA x 1024 threads per SM
+#define NLOS_FWD_ONE_CTA 1                  // standalone forward: 1 CTA x 1024 threads per SM
 #endif
 #ifndef NLOS_FWD_WS
 #define NLOS_FWD_WS 1                       // standalone forward: warp-specialised staging
+#endif
+#ifndef NLOS_FWD_SQRT_RCP
+#define NLOS_FWD_SQRT_RCP 1                 // r from sqrt.approx, weights from one rcp.approx
+#endif
+#ifndef NLOS_FWD_EARLY
+#define NLOS_FWD_EARLY 1                    // warp-uniform early out before the square roots
+#endif
+#ifndef NLOS_FWD_VOTE
+#define NLOS_FWD_VOTE 0                     // 2: warp-uniform skip before the reductions
 #endif
 #ifndef NLOS_FWD_STAGES
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
 #endif
 
-enum { MODE_NEAREST = 0, MODE_NEAREST_COUNT = 1, MODE_SPLAT = 2 };
+enum { MODE_NEAREST = 0, MODE_NEAREST_COUNT = 1, MODE_SPLAT = 2, MODE_SPLAT_MOM = 3 };
+
+// Moment form of the splat (standalone forward, sigma >= 2.5 bins): per bin m
+// and scan point, M_n[m] = sum of w c^n over the pairs with floor(u) = m,
+// c = 1/2 - (u - m), n < kMoments; at flush time
+//   tau[b] = sum_n sum_j D_n[j] M_n[b - j],  D_n[j] = K^(n)(j) / n!,
+// the Taylor expansion of the Gaussian K(j + c) about the bin offset j. With
+// 6 moments the truncation error is below 2e-6 of the kernel's peak for sigma
+// >= 2.5 (3e-7 at sigma = 3.2). Each moment histogram has kMomRows rows
+// (window bins plus J on each side).
+constexpr int kMoments = 6;
+constexpr int kMomRows = 256;
+constexpr int kMomMaxJ = 60;
+constexpr uint32_t kMomStride = kMomRows * 32 * 4;  // bytes between moment histograms
+struct MomTab {
+  int J;                                  // taps j = -J..J
+  float d[kMoments][2 * kMomMaxJ + 1];    // D_n[j + J]
+};
+
+// Fills mt for the unit-area Gaussian of standard deviation s bins (host).
+void moment_table(double s, MomTab& mt);
+
+// The moment form is used for splat kernels of at least 2.5 bins standard
+// deviation (truncation error <= 1.3e-6 of the peak) whose taps fit MomTab.
+inline bool use_moments(double sigma) {
+  return sigma >= 2.5 && (int)std::ceil(6.0 * sigma) + 1 <= kMomMaxJ;
+}
+
+// Per-thread counters of one forward run, added to the scene scratch at exit.
+struct FwdCount {
+  unsigned long long boundary = 0;  // pairs within eps of a bin edge (count mode)
+  unsigned long long full = 0;      // warp iterations past the early out (x 64 pairs)
+};
 
 struct FwdArgs {
   const PointPair* pairs;
@@ -52,6 +95,7 @@ struct FwdArgs {
   float* tau;
   unsigned int* err;
   unsigned long long* boundary;
+  unsigned long long* pairs_full;  // pairs past the early out (scene scratch)
   unsigned long long units;   // standalone launch: total units
   uint32_t n_pairs, S, B, bw, n_win, n_blk, ppb;
   uint32_t stages;   // staged point blocks (standalone warp-specialised kernel)
@@ -65,6 +109,10 @@ struct FwdArgs {
   float taps[kMaxTaps];
 };
 
+struct bool2_t {
+  bool x, y;
+};
+
 // Path-bin coordinate u and weight w of the two points of a pair for one scan
 // spot (sx, sy, 0) with bin offset off (FP32x2: component i = point i).
 //   r^2 = (px - sx)^2 + (py - sy)^2 + pz^2,   u = r * kbin + off (+ uoff)
@@ -73,14 +121,52 @@ struct FwdArgs {
 // Weight by scan and cosine mode (per-point factors folded in at packing):
 //   confocal    NONE: kq / r^4        OBJECT: (cn / r^3)^2   WALL: (cn / r^4)^2
 //   non-confocal NONE: kq / r^2       OBJECT: cn / r^3       WALL: cn / r^4
-template <int SCAN, int COS>
-__device__ __forceinline__ void pair_eval2(const PointPair& q, float2 nsx, float2 nsy, float2 sx,
-                                           float2 sy, float2 off, float2 kbin, float2& u,
-                                           float2& w, float2& cn) {
-  float2 dx = __fadd2_rn(q.px, nsx);
-  float2 dy = __fadd2_rn(q.py, nsy);
-  float2 r2 = __ffma2_rn(dx, dx, q.pz2);
+// Split in two: pair_geom2 (r^2 and cn: differences and FMAs only) and
+// pair_finish2 (square root, u and the weight), so that the caller can skip
+// the second part when no lane of the warp can bin either point.
+__device__ __forceinline__ void pair_geom2(const PointPair& q, float2 nsx, float2 nsy, float2& r2,
+                                           float2& cn) {
+  const float2 dx = __fadd2_rn(q.px, nsx);
+  const float2 dy = __fadd2_rn(q.py, nsy);
+  r2 = __ffma2_rn(dx, dx, q.pz2);
   r2 = __ffma2_rn(dy, dy, r2);
+  cn = __ffma2_rn(q.na, dx, q.nc);
+  cn = __ffma2_rn(q.nb, dy, cn);
+}
+
+template <int SCAN, int COS>
+__device__ __forceinline__ void pair_finish2(const PointPair& q, float2 r2, float2 cn, float2 off,
+                                             float2 kbin, float2& u, float2& w) {
+  const float2 o = (SCAN == NLOS_CONFOCAL) ? off : __fadd2_rn(off, q.uoff);
+#if NLOS_FWD_SQRT_RCP
+  // r from the hardware square root; the weight's inverse powers of r from a
+  // single reciprocal of r^2k, so no approximation error is raised to a power
+  const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
+  u = __ffma2_rn(r, kbin, o);
+  if (SCAN == NLOS_CONFOCAL) {
+    if (COS == NLOS_COS_NONE) {
+      const float2 d = __fmul2_rn(r2, r2);
+      w = __fmul2_rn(q.kq, make_float2(rcp_approx(d.x), rcp_approx(d.y)));
+    } else if (COS == NLOS_COS_OBJECT) {
+      const float2 d = __fmul2_rn(__fmul2_rn(r2, r2), r2);
+      w = __fmul2_rn(__fmul2_rn(cn, cn), make_float2(rcp_approx(d.x), rcp_approx(d.y)));
+    } else {
+      const float2 d2 = __fmul2_rn(r2, r2);
+      const float2 d = __fmul2_rn(d2, d2);
+      w = __fmul2_rn(__fmul2_rn(cn, cn), make_float2(rcp_approx(d.x), rcp_approx(d.y)));
+    }
+  } else {
+    if (COS == NLOS_COS_NONE) {
+      w = __fmul2_rn(q.kq, make_float2(rcp_approx(r2.x), rcp_approx(r2.y)));
+    } else if (COS == NLOS_COS_OBJECT) {
+      const float2 d = __fmul2_rn(r2, r);
+      w = __fmul2_rn(cn, make_float2(rcp_approx(d.x), rcp_approx(d.y)));
+    } else {
+      const float2 d = __fmul2_rn(r2, r2);
+      w = __fmul2_rn(cn, make_float2(rcp_approx(d.x), rcp_approx(d.y)));
+    }
+  }
+#else
   float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
   // one Newton step on 1/r (e = 1 - r2 ri^2, ri += ri e / 2): the hardware
   // estimate's few-ulp error would otherwise grow to ~1e-6 in the r^-6 weight
@@ -88,10 +174,7 @@ __device__ __forceinline__ void pair_eval2(const PointPair& q, float2 nsx, float
   const float2 e = __ffma2_rn(make_float2(-r.x, -r.y), ri, make_float2(1.0f, 1.0f));
   ri = __ffma2_rn(__fmul2_rn(ri, make_float2(0.5f, 0.5f)), e, ri);
   r = __fmul2_rn(r2, ri);
-  float2 o = (SCAN == NLOS_CONFOCAL) ? off : __fadd2_rn(off, q.uoff);
   u = __ffma2_rn(r, kbin, o);
-  cn = __ffma2_rn(q.na, dx, q.nc);
-  cn = __ffma2_rn(q.nb, dy, cn);
   float2 ri2 = __fmul2_rn(ri, ri);
   if (SCAN == NLOS_CONFOCAL) {
     if (COS == NLOS_COS_NONE) {
@@ -111,6 +194,37 @@ __device__ __forceinline__ void pair_eval2(const PointPair& q, float2 nsx, float
     } else {
       w = __fmul2_rn(cn, __fmul2_rn(ri2, ri2));
     }
+  }
+#endif
+}
+
+template <int SCAN, int COS>
+__device__ __forceinline__ void pair_eval2(const PointPair& q, float2 nsx, float2 nsy, float2 off,
+                                           float2 kbin, float2& u, float2& w, float2& cn) {
+  float2 r2;
+  pair_geom2(q, nsx, nsy, r2, cn);
+  pair_finish2<SCAN, COS>(q, r2, cn, off, kbin, u, w);
+}
+
+// Early-out test on r^2, before any square root: can the point land in
+// [-margin, lim + margin) bins of the window for this lane? Conservative
+// (margin >= 1 bin against a rounding error of ~1e-3 bin); the exact bin
+// test follows for the points that pass.
+//   confocal:     r in [r_lo, r_hi) with per-lane bounds (r2lo, r2hi = squares)
+//   non-confocal: r_lo/hi = base_lo/hi - uoff / kbin (per point and lane)
+template <int SCAN>
+__device__ __forceinline__ bool2_t may_bin2(const PointPair& q, float2 r2, float2 r2lo, float2 r2hi,
+                                            float2 ikbin_neg) {
+  if (SCAN == NLOS_CONFOCAL) {
+    return bool2_t{r2.x >= r2lo.x && r2.x < r2hi.x, r2.y >= r2lo.y && r2.y < r2hi.y};
+  } else {
+    // here r2lo / r2hi hold base_lo / base_hi (in metres, per lane)
+    const float2 rlo = __ffma2_rn(q.uoff, ikbin_neg, r2lo);
+    const float2 rhi = __ffma2_rn(q.uoff, ikbin_neg, r2hi);
+    const float2 lo2 = __fmul2_rn(rlo, rlo);
+    const float2 hi2 = __fmul2_rn(rhi, rhi);
+    return bool2_t{rhi.x > 0.f && r2.x < hi2.x && (rlo.x <= 0.f || r2.x >= lo2.x),
+                   rhi.y > 0.f && r2.y < hi2.y && (rlo.y <= 0.f || r2.y >= lo2.y)};
   }
 }
 
@@ -134,7 +248,9 @@ __device__ __forceinline__ bool facing(float cn) {
 
 // One point's Gaussian splat into this lane's histogram column (bins of the
 // window with |b + 1/2 - u| < 6 sigma), taps by the recurrence
-// K_{b+1} = K_b * rho_b, rho_{b+1} = rho_b * exp(-1/sigma^2).
+// K_{b+1} = K_b * rho_b, rho_{b+1} = rho_b * exp(-1/sigma^2), restarted from a
+// direct evaluation every 8 taps: the recurrence's rounding error grows with
+// the square of the number of steps (about 1e-4 after 90 taps in FP32).
 __device__ __forceinline__ void splat_one(uint32_t col_addr, float u, float w, int lim,
                                           const FwdArgs& a) {
   float lo_f = floorf(u - 0.5f - a.reach) + 1.0f;
@@ -142,11 +258,15 @@ __device__ __forceinline__ void splat_one(uint32_t col_addr, float u, float w, i
   int lo = max(0, (int)lo_f);
   int hi = min(lim - 1, (int)hi_f);
   if (lo > hi) return;
-  float x0 = (float)lo + 0.5f - u;
-  float K = w * a.norm * expf(-x0 * x0 * a.inv2s2);
-  float rho = expf(-(2.0f * x0 + 1.0f) * a.inv2s2);
+  const float wn = w * a.norm;
   uint32_t addr = col_addr + (uint32_t)lo * (kTile * 4);
+  float K = 0.f, rho = 0.f;
   for (int b = lo; b <= hi; ++b) {
+    if (((b - lo) & 7) == 0) {
+      const float x = (float)b + 0.5f - u;
+      K = wn * expf(-x * x * a.inv2s2);
+      rho = expf(-(2.0f * x + 1.0f) * a.inv2s2);
+    }
     red_add_shared(addr, K);
     K *= rho;
     rho *= a.qstep;
@@ -167,10 +287,20 @@ struct TileState {
   uint32_t w0 = 0;
   int lim = 0;  // bins of the current window that lie inside [0, B)
   float2 sx2, sy2, nsx2, nsy2, off2;
+  float2 r2lo2, r2hi2;  // early-out bounds (see may_bin2)
 };
 
+// Bins beyond the window edges that still matter: 1 for the histogram modes
+// (edge pairs of the boundary count), the splat reach + 1, J + 1 for moments.
+template <int MODE>
+__device__ __forceinline__ float window_margin(const FwdArgs& a, int mom_J) {
+  return MODE == MODE_SPLAT ? a.reach + 1.0f
+         : MODE == MODE_SPLAT_MOM ? (float)(mom_J + 1)
+                                  : 1.0f;
+}
+
 __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int lane,
-                                          TileState& ts) {
+                                          TileState& ts, bool confocal, float margin) {
   const uint32_t tile = (uint32_t)(tw / a.n_win);
   ts.tw = tw;
   ts.w0 = (uint32_t)(tw % a.n_win) * a.bw;
@@ -184,9 +314,24 @@ __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int la
     ts.nsy2 = make_float2(-sp.sy, -sp.sy);
     const float o = sp.off - (float)ts.w0;
     ts.off2 = make_float2(o, o);
+    // r range of u in [-margin, lim + margin): r = (u - o) / kbin
+    const float ik = 1.0f / a.kbin;
+    const float rlo = (-margin - o) * ik, rhi = ((float)ts.lim + margin - o) * ik;
+    float lo, hi;
+    if (confocal) {
+      lo = rlo > 0.f ? rlo * rlo : 0.f;
+      hi = rhi > 0.f ? rhi * rhi : -1.f;
+    } else {
+      lo = rlo;  // the point's uoff / kbin is subtracted in may_bin2
+      hi = rhi;
+    }
+    ts.r2lo2 = make_float2(lo, lo);
+    ts.r2hi2 = make_float2(hi, hi);
   } else {
     ts.sx2 = ts.sy2 = ts.nsx2 = ts.nsy2 = make_float2(0.f, 0.f);
     ts.off2 = make_float2(-1e30f, -1e30f);  // u -> -inf: never binned
+    ts.r2lo2 = make_float2(1.f, 1.f);      // empty r ranges
+    ts.r2hi2 = make_float2(-1.f, -1.f);
   }
 }
 
@@ -235,27 +380,110 @@ __device__ __forceinline__ void flush_tile(const FwdArgs& a, long long tw, const
 // All pairs of one staged block for this warp (pairs warp_rel, warp_rel +
 // n_warps, ...): evaluate both points of a pair for the lane's scan point and
 // add their weights to the lane's histogram column (or splat them).
+// red.shared.add.f32 [addr + k * kMomStride] of w c^k for the moments k <
+// kMoments of one point, predicated on row < rows and a facing cosine.
+template <int K>
+__device__ __forceinline__ void red_moment(uint32_t addr, float wk, uint32_t ok) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %2, 0;\n @p red.shared.add.f32 [%0+%3], %1;\n}\n" ::"r"(addr),
+      "f"(wk), "r"(ok), "n"(K * kMomStride)
+      : "memory");
+}
+
+template <int COS>
+__device__ __forceinline__ void red_moments(uint32_t addr, float w, float c, uint32_t row,
+                                            uint32_t rows, float cn) {
+  static_assert(kMoments == 6, "red_moments is written out for six moments");
+  const uint32_t ok = (row < rows && (COS == NLOS_COS_NONE || cn > 0.0f)) ? 1u : 0u;
+  float wk = w;
+  red_moment<0>(addr, wk, ok);
+  wk *= c;
+  red_moment<1>(addr, wk, ok);
+  wk *= c;
+  red_moment<2>(addr, wk, ok);
+  wk *= c;
+  red_moment<3>(addr, wk, ok);
+  wk *= c;
+  red_moment<4>(addr, wk, ok);
+  wk *= c;
+  red_moment<5>(addr, wk, ok);
+}
+
 template <int SCAN, int COS, int MODE>
 __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair* blkp, uint32_t n,
                                               int warp_rel, int n_warps, const TileState& ts,
-                                              uint32_t col_addr, unsigned long long& nboundary) {
+                                              uint32_t col_addr, FwdCount& cnt,
+                                              int mom_J = 0) {
   const float2 kbin2 = make_float2(a.kbin, a.kbin);
   const float2 magic2 = make_float2(kMagic, kMagic);
+  const float2 ikbin_neg = make_float2(-1.0f / a.kbin, -1.0f / a.kbin);
 #pragma unroll 2
   for (uint32_t i = warp_rel; i < n; i += n_warps) {
     PointPair q;
     load_pair(blkp + i, q);
-    float2 u, w, cn;
-    pair_eval2<SCAN, COS>(q, ts.nsx2, ts.nsy2, ts.sx2, ts.sy2, ts.off2, kbin2, u, w, cn);
+    float2 r2, cn;
+    pair_geom2(q, ts.nsx2, ts.nsy2, r2, cn);
+#if NLOS_FWD_EARLY
+    // warp-uniform early out: for most (tile, point) combinations of a
+    // scene no lane can bin either point (outside the window or facing away)
+    // (the boundary count takes every pair near a bin edge, facing or not)
+    const bool2_t m = may_bin2<SCAN>(q, r2, ts.r2lo2, ts.r2hi2, ikbin_neg);
+    const bool fa = MODE == MODE_NEAREST_COUNT || facing<COS>(cn.x);
+    const bool fb = MODE == MODE_NEAREST_COUNT || facing<COS>(cn.y);
+    if (!__any_sync(0xffffffffu, (m.x && fa) || (m.y && fb))) continue;
+#endif
+    ++cnt.full;
+    float2 u, w;
+    pair_finish2<SCAN, COS>(q, r2, cn, ts.off2, kbin2, u, w);
     if (MODE == MODE_SPLAT) {
       if (facing<COS>(cn.x)) splat_one(col_addr, u.x, w.x, ts.lim, a);
       if (facing<COS>(cn.y)) splat_one(col_addr, u.y, w.y, ts.lim, a);
+    } else if (MODE == MODE_SPLAT_MOM) {
+      const float2 t = __fadd2_rd(u, magic2);                        // kMagic + floor(u)
+      const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));  // floor(u), exact
+      const float2 fr = __fadd2_rn(u, make_float2(-fl.x, -fl.y));      // u - floor(u), exact
+      const float2 c = __fadd2_rn(make_float2(0.5f, 0.5f), make_float2(-fr.x, -fr.y));
+      const uint32_t ra = (uint32_t)(__float_as_int(t.x) - kMagicBits + mom_J);
+      const uint32_t rb = (uint32_t)(__float_as_int(t.y) - kMagicBits + mom_J);
+      const uint32_t rows = (uint32_t)(a.bw + 2 * mom_J);
+#if NLOS_FWD_VOTE == 2
+      // one warp-uniform test first: most pairs of a tile fall outside the
+      // window or face away together
+      const bool oka = ra < rows && facing<COS>(cn.x);
+      const bool okb = rb < rows && facing<COS>(cn.y);
+      if (__any_sync(0xffffffffu, oka || okb)) {
+        red_moments<COS>(col_addr + ra * (kTile * 4), w.x, c.x, ra, rows, cn.x);
+        red_moments<COS>(col_addr + rb * (kTile * 4), w.y, c.y, rb, rows, cn.y);
+      }
+#else
+      red_moments<COS>(col_addr + ra * (kTile * 4), w.x, c.x, ra, rows, cn.x);
+      red_moments<COS>(col_addr + rb * (kTile * 4), w.y, c.y, rb, rows, cn.y);
+#endif
     } else {
       const float2 t = __fadd2_rd(u, magic2);  // kMagic + floor(u), exactly
       const uint32_t ba = (uint32_t)(__float_as_int(t.x) - kMagicBits);
       const uint32_t bb = (uint32_t)(__float_as_int(t.y) - kMagicBits);
       const uint32_t aa = col_addr + ba * (kTile * 4);
       const uint32_t ab = col_addr + bb * (kTile * 4);
+      // the in-window and facing test and the reduction in one predicated
+      // block (shared f32 reductions are a compare-and-swap loop here)
+#if NLOS_FWD_VOTE == 2
+      // preceded by one warp-uniform test: most pairs of a tile fall outside
+      // the window or face away together
+      const bool oka = ba < (uint32_t)ts.lim && facing<COS>(cn.x);
+      const bool okb = bb < (uint32_t)ts.lim && facing<COS>(cn.y);
+#endif
+#if NLOS_FWD_VOTE == 2
+      if (__any_sync(0xffffffffu, oka || okb)) {
+        if (COS == NLOS_COS_NONE) {
+          red_add_shared_if_bin(aa, w.x, ba, (uint32_t)ts.lim);
+          red_add_shared_if_bin(ab, w.y, bb, (uint32_t)ts.lim);
+        } else {
+          red_add_shared_if_bin_cos(aa, w.x, ba, (uint32_t)ts.lim, cn.x);
+          red_add_shared_if_bin_cos(ab, w.y, bb, (uint32_t)ts.lim, cn.y);
+        }
+      }
+#else
       if (COS == NLOS_COS_NONE) {
         red_add_shared_if_bin(aa, w.x, ba, (uint32_t)ts.lim);
         red_add_shared_if_bin(ab, w.y, bb, (uint32_t)ts.lim);
@@ -263,6 +491,7 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
         red_add_shared_if_bin_cos(aa, w.x, ba, (uint32_t)ts.lim, cn.x);
         red_add_shared_if_bin_cos(ab, w.y, bb, (uint32_t)ts.lim, cn.y);
       }
+#endif
       if (MODE == MODE_NEAREST_COUNT && ts.w0 == 0) {
         // pairs with u within eps of a bin edge m in [0, B] (u is global here)
         const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));
@@ -273,7 +502,47 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
                         (1.0f - fb < a.eps && fl.y + 1.0f >= 0.f && fl.y + 1.0f <= (float)a.B);
         // the odd slot of the last pair may be padding (pz2 huge): its u is
         // never near a valid edge
-        nboundary += (unsigned)na + (unsigned)nb;
+        cnt.boundary += (unsigned)na + (unsigned)nb;
+      }
+    }
+  }
+}
+
+// Moment flush: out[o] = sum_n sum_j D_n[j] M_n[o - w0 - j + J] for the bins o
+// of the window inside [0, B); four bins per thread, one vector reduction.
+__device__ __forceinline__ void flush_tile_mom(const FwdArgs& a, const MomTab& mt, long long tw,
+                                               const float* hist, int warp_rel, int n_warps) {
+  const uint32_t tile = (uint32_t)(tw / a.n_win);
+  const uint32_t win = (uint32_t)(tw % a.n_win);
+  const int w0 = (int)(win * a.bw);
+  const int lim = (int)min(a.bw, a.B - (uint32_t)w0);
+  const int J = mt.J;
+  const int nq = (lim + 3) >> 2;
+  const int c = threadIdx.x & 31;
+  const uint32_t s = tile * kTile + c;
+  for (int qi = warp_rel; qi < nq; qi += n_warps) {
+    const int r0 = 4 * qi;  // window-relative output bin
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < kMoments; ++k) {
+      const float* mk = hist + (size_t)k * kMomRows * kTile;
+      const float* dk = mt.d[k];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float acc = v[e];
+        // row of tap j: (r0 + e) - j + J, j = -J..J
+        for (int j = -J; j <= J; ++j) acc = fmaf(dk[j + J], mk[(r0 + e - j + J) * kTile + c], acc);
+        v[e] = acc;
+      }
+    }
+    const int o0 = w0 + r0;
+    if (s < a.S && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)) {
+      float* dst = a.tau + (size_t)s * a.B + o0;
+      if ((a.B & 3u) == 0u && (o0 & 3) == 0) {
+        red_add_global_v4(dst, make_float4(v[0], v[1], v[2], v[3]));
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (r0 + e < lim) red_add_global(dst + e, v[e]);
       }
     }
   }
@@ -298,7 +567,7 @@ __device__ __forceinline__ void issue_block(const FwdArgs& a, const FwdSmem& sm,
 // *a.err); every thread returns the same value.
 template <int SCAN, int COS, int MODE>
 __device__ bool fwd_run(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
-                        const FwdSmem& sm, uint32_t& it_base, unsigned long long& nboundary) {
+                        const FwdSmem& sm, uint32_t& it_base, FwdCount& cnt) {
   float* hist = sm.hist;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -323,7 +592,7 @@ __device__ bool fwd_run(const FwdArgs& a, unsigned long long u0, unsigned long l
         __syncthreads();
       }
       for (uint32_t i = tid; i < a.bw * kTile; i += blockDim.x) hist[i] = 0.f;
-      load_tile(a, tw, lane, ts);
+      load_tile(a, tw, lane, ts, SCAN == NLOS_CONFOCAL, window_margin<MODE>(a, 0));
       __syncthreads();
     }
     const bool ok = mbar_wait_bounded(&sm.bars[slot], parity);
@@ -337,7 +606,7 @@ __device__ bool fwd_run(const FwdArgs& a, unsigned long long u0, unsigned long l
     }
     const uint32_t first = blk * a.ppb;
     compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb, min(a.ppb, a.n_pairs - first),
-                                   warp, nwarps, ts, col_addr, nboundary);
+                                   warp, nwarps, ts, col_addr, cnt);
     __syncthreads();
     if (tid == 0 && unit + 2 < u1) {
       fence_proxy_async_smem();
@@ -369,7 +638,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // their work but keep arriving, so no barrier is left waiting.
 template <int SCAN, int COS, int MODE>
 __device__ void fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
-                           const FwdSmem& sm, int stages, unsigned long long& nboundary) {
+                           const FwdSmem& sm, int stages, FwdCount& cnt,
+                           const MomTab* mt = nullptr) {
+  const int mom_J = (MODE == MODE_SPLAT_MOM) ? mt->J : 0;
+  const uint32_t hist_words = (MODE == MODE_SPLAT_MOM) ? (uint32_t)kMoments * kMomRows * kTile
+                                                       : a.bw * kTile;
   __shared__ int s_abort;
   float* hist = sm.hist;
   const int tid = threadIdx.x;
@@ -414,11 +687,12 @@ __device__ void fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
       if (tw != ts.tw) {
         named_barrier(1, nthr);  // every consumer is done with the previous tile
         if (ts.tw >= 0) {
-          flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+          if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
+          else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
           named_barrier(1, nthr);
         }
-        for (uint32_t i = tid - 32; i < a.bw * kTile; i += nthr) hist[i] = 0.f;
-        load_tile(a, tw, lane, ts);
+        for (uint32_t i = tid - 32; i < hist_words; i += nthr) hist[i] = 0.f;
+        load_tile(a, tw, lane, ts, SCAN == NLOS_CONFOCAL, window_margin<MODE>(a, mom_J));
         named_barrier(1, nthr);
       }
       const bool aborted = *(volatile int*)&s_abort != 0;
@@ -427,7 +701,7 @@ __device__ void fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
           const uint32_t first = blk * a.ppb;
           compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb,
                                          min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
-                                         nboundary);
+                                         cnt, mom_J);
         } else if (lane == 0) {
           atomicOr(a.err, kErrWaitTimeout);
           s_abort = 1;
@@ -437,7 +711,8 @@ __device__ void fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
       if (lane == 0) mbar_arrive(&empty[slot]);
     }
     named_barrier(1, nthr);
-    flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+    if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
+    else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
   }
   __syncthreads();
 }

@@ -32,6 +32,8 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -58,11 +60,12 @@ constexpr uint64_t kRing = 1ull << 16;      // work-item ring slots
 constexpr int kMaxJobs = 1024;               // concurrently admitted requests
 constexpr uint32_t kCapBw = 1024;            // histogram bins per window in the serving kernel
 constexpr uint32_t kPackChunk = 16384;       // pairs per PACK item
-constexpr uint64_t kZeroChunk = 1ull << 20;  // floats per ZERO item
-constexpr uint32_t kFwdChunk = 16;           // point blocks per FORWARD item
+constexpr uint64_t kZeroChunk = 1ull << 18;  // floats per ZERO item
+constexpr uint32_t kFwdChunk = 32;           // point blocks per FORWARD item
+constexpr uint64_t kWindowPerSm = 16;        // items outstanding per SM (publication window)
 constexpr uint64_t kMaxPhaseItems = 16384;   // FORWARD items per request (coarser beyond)
 constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
-constexpr uint64_t kNoiseChunk = 1ull << 18; // bins per NOISE item
+constexpr uint64_t kNoiseChunk = 1ull << 15; // bins per NOISE item
 constexpr long long kIdleCycles = 2000000000LL;  // ~1 s without work: exit
 constexpr int kServeThreads = 512;            // 16 warps: room for the registers of every fused path
 constexpr uint64_t kNone = ~0ull;
@@ -83,11 +86,13 @@ struct __align__(16) JobDesc {
 static_assert(sizeof(JobDesc) % 16 == 0, "JobDesc copies as int4");
 
 struct __align__(32) WorkItem {
-  uint32_t job;
-  uint32_t kind;
+  uint16_t job;   // slot of the request
+  uint16_t kind;
+  uint32_t gen;   // the request's ticket (low bits): tells slot reuses apart
   uint64_t begin, end;
   uint64_t seq;  // == ring index once the slot is published
 };
+static_assert(sizeof(WorkItem) == 32, "work item layout");
 
 struct Control {
   uint64_t tail;       // items published (host)
@@ -124,9 +129,11 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
 template <int SCAN, int COS>
 __device__ bool fwd_item_mode(const FwdArgs& a, uint64_t b, uint64_t e, const FwdSmem& sm,
                               uint32_t& it, int bin_mode) {
-  unsigned long long nb = 0;
-  if (bin_mode == NLOS_BIN_SPLAT) return fwd_run<SCAN, COS, MODE_SPLAT>(a, b, e, sm, it, nb);
-  return fwd_run<SCAN, COS, MODE_NEAREST>(a, b, e, sm, it, nb);
+  FwdCount cnt;
+  const bool ok = bin_mode == NLOS_BIN_SPLAT ? fwd_run<SCAN, COS, MODE_SPLAT>(a, b, e, sm, it, cnt)
+                                             : fwd_run<SCAN, COS, MODE_NEAREST>(a, b, e, sm, it, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
+  return ok;
 }
 
 __device__ bool fwd_item(const JobDesc& j, uint64_t b, uint64_t e, const FwdSmem& sm,
@@ -208,6 +215,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
   }
   __syncthreads();
   uint32_t it = 0;
+  uint32_t cached_job = 0xFFFFFFFFu, cached_gen = 0;
 
   for (;;) {
     if (tid == 0) {
@@ -258,14 +266,17 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       continue;
     }
     const WorkItem item = s_item;
-    // job descriptor: mapped memory -> shared memory
-    {
+    // job descriptor: mapped memory -> shared memory, unless this CTA holds
+    // it already (consecutive items mostly belong to one request; a slot's
+    // descriptor only changes with a new request, i.e. a new gen)
+    if (item.job != cached_job || item.gen != cached_gen) {
       const int4* src = reinterpret_cast<const int4*>(q.jobs + item.job);
       int4* dst = reinterpret_cast<int4*>(jd);
       for (int i = tid; i < (int)(sizeof(JobDesc) / 16); i += blockDim.x) dst[i] = src[i];
+      cached_job = item.job;
+      cached_gen = item.gen;
+      __syncthreads();
     }
-    __syncthreads();
-    bool ok = true;
     switch (item.kind) {
       case K_PACK:
         for (uint64_t k = item.begin + tid; k < item.end; k += blockDim.x)
@@ -276,7 +287,8 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         for (uint64_t k = item.begin + tid; k < item.end; k += blockDim.x) jd->fwd.tau[k] = 0.0f;
         break;
       case K_FWD:
-        ok = fwd_item(*jd, item.begin, item.end, sm, it);
+        // a forward wait that gave up is recorded in the job error word
+        (void)fwd_item(*jd, item.begin, item.end, sm, it);
         break;
       case K_REDUCE:
         reduce_item(*jd, item.begin, item.end);
@@ -285,7 +297,6 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         noise_item(*jd, item.begin, item.end);
         break;
     }
-    (void)ok;  // a forward wait that gave up is recorded in the job error word
     __syncthreads();
     if (tid == 0) {
       __threadfence_system();
@@ -320,7 +331,7 @@ struct Request {
   float* tau = nullptr;
   uint32_t* counts = nullptr;
   SceneScratch* scratch = nullptr;
-  SceneScratch* h_scratch = nullptr;  // pinned copy at completion
+  SceneScratch* h_scratch = nullptr;  // pinned copy at completion (the slot's pool entry)
   cudaEvent_t ev = nullptr;
   int phase = 0;
   uint32_t items[4] = {0, 0, 0, 0};
@@ -330,6 +341,8 @@ struct Request {
   uint64_t first_item = 0, last_item = 0;
   bool release_on_done = false;
   Clock::time_point t_submit, t_done;
+  Clock::time_point t_mark[8];  // tracing: admit, upload done, phase 0..3 done, finish
+  uint32_t items_total = 0;
   nlos_stats stats{};
 };
 
@@ -350,12 +363,18 @@ struct Server {
   WorkItem* ring = nullptr;
   JobDesc* jobs = nullptr;
   JobStatus* status = nullptr;
+  // pinned per-slot copies of the request scratch at completion; allocated
+  // once, because cudaFreeHost waits for all device work (the persistent
+  // kernel included) and cudaHostAlloc may synchronise too
+  SceneScratch* h_scratch = nullptr;
   ServeArgs dev_args{};         // device addresses of the same memory
   unsigned long long* d_head = nullptr;
   uint64_t published = 0;
+  uint64_t window = 0;          // items outstanding on the device at most
   bool kernel_running = false;
   cudaEvent_t kernel_done = nullptr;
   size_t smem = 0;
+  FILE* trace = nullptr;  // NLOS_SERVE_TRACE
   // fault injection (tests)
   int inject = 0;
   uint64_t withheld_item = kNone;
@@ -399,6 +418,7 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   a.tau = r->tau;
   a.err = &r->scratch->err;
   a.boundary = &r->scratch->boundary_pairs;
+  a.pairs_full = &r->scratch->pairs_full;
   a.n_pairs = (uint32_t)((g.P + 1) / 2);
   a.S = (uint32_t)g.S;
   a.B = g.B;
@@ -441,22 +461,18 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   (void)sv;
 }
 
-// Writes as many backlog items of r as the ring has room for and moves the
-// tail (release). At most half the ring is outstanding at any time (see the
-// claim protocol), so a large phase is published over several passes.
-void publish_some(Server& sv, Request* r) {
-  const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
-  const uint64_t outstanding = sv.published - completed;
-  if (outstanding >= kRing / 2) return;
-  const size_t room = (size_t)(kRing / 2 - outstanding);
-  const size_t n = std::min(room, r->backlog.size() - r->backlog_pos);
-  if (n == 0) return;
+// Writes up to max_items backlog items of r into the ring and moves the tail
+// (release); returns how many it wrote.
+size_t publish_some(Server& sv, Request* r, size_t max_items) {
+  const size_t n = std::min(max_items, r->backlog.size() - r->backlog_pos);
+  if (n == 0) return 0;
   uint64_t idx = sv.published;
   for (size_t k = 0; k < n; ++k) {
     const WorkItem& w = r->backlog[r->backlog_pos + k];
     WorkItem* slot = sv.ring + (idx % kRing);
     slot->job = w.job;
     slot->kind = w.kind;
+    slot->gen = w.gen;
     slot->begin = w.begin;
     slot->end = w.end;
     if (sv.inject == 1 && sv.withheld_item == kNone) {
@@ -480,19 +496,38 @@ void publish_some(Server& sv, Request* r) {
     r->backlog.shrink_to_fit();
     r->backlog_pos = 0;
   }
+  return n;
+}
+
+// Oldest request first: publishes backlog items of the running requests in
+// admission order while fewer than sv.window items are outstanding on the
+// device. Younger requests only fill what the older ones leave of the
+// window (their phase transitions, their last items), so a request's
+// latency is close to running it alone after the ones before it, while the
+// device stays busy. The window (a few items per SM) stays far below half
+// the ring, which the claim protocol requires.
+void publish_window(Server& sv) {
+  const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
+  uint64_t outstanding = sv.published - completed;
+  for (Request* r : sv.active) {
+    if (outstanding >= sv.window) break;
+    if (r->state != R_RUNNING || r->backlog.empty()) continue;
+    outstanding += publish_some(sv, r, (size_t)(sv.window - outstanding));
+  }
 }
 
 void publish_phase(Server& sv, Request* r, int phase) {
   const Geometry& g = r->g;
   std::vector<WorkItem> items;
-  const uint32_t job = (uint32_t)r->slot;
+  const uint16_t job = (uint16_t)r->slot;
+  const uint32_t gen = (uint32_t)r->ticket;
   if (phase == PH_PREP) {
     const uint64_t n_pairs = (g.P + 1) / 2;
     for (uint64_t b = 0; b < n_pairs; b += kPackChunk)
-      items.push_back({job, K_PACK, b, std::min<uint64_t>(n_pairs, b + kPackChunk), 0});
+      items.push_back({job, K_PACK, gen, b, std::min<uint64_t>(n_pairs, b + kPackChunk), 0});
     const uint64_t n = g.S * (uint64_t)g.B;
     for (uint64_t b = 0; b < n; b += kZeroChunk)
-      items.push_back({job, K_ZERO, b, std::min<uint64_t>(n, b + kZeroChunk), 0});
+      items.push_back({job, K_ZERO, gen, b, std::min<uint64_t>(n, b + kZeroChunk), 0});
   } else if (phase == PH_FWD) {
     // point blocks per item: kFwdChunk, coarser for very large requests so a
     // phase stays within kMaxPhaseItems (an item never spans two (tile, window))
@@ -502,20 +537,39 @@ void publish_phase(Server& sv, Request* r, int phase) {
     while (chunk < a.n_blk && tws * ((a.n_blk + chunk - 1) / chunk) > kMaxPhaseItems) chunk *= 2;
     for (uint64_t tw = 0; tw < tws; ++tw)
       for (uint64_t b = 0; b < a.n_blk; b += chunk)
-        items.push_back({job, K_FWD, tw * a.n_blk + b, tw * a.n_blk + std::min<uint64_t>(a.n_blk, b + chunk), 0});
+        items.push_back({job, K_FWD, gen, tw * a.n_blk + b, tw * a.n_blk + std::min<uint64_t>(a.n_blk, b + chunk), 0});
   } else if (phase == PH_REDUCE) {
     for (uint64_t b = 0; b < g.S; b += kReduceChunk)
-      items.push_back({job, K_REDUCE, b, std::min<uint64_t>(g.S, b + kReduceChunk), 0});
+      items.push_back({job, K_REDUCE, gen, b, std::min<uint64_t>(g.S, b + kReduceChunk), 0});
   } else {
     const uint64_t n = g.S * (uint64_t)g.B;
     for (uint64_t b = 0; b < n; b += kNoiseChunk)
-      items.push_back({job, K_NOISE, b, std::min<uint64_t>(n, b + kNoiseChunk), 0});
+      items.push_back({job, K_NOISE, gen, b, std::min<uint64_t>(n, b + kNoiseChunk), 0});
   }
   r->phase = phase;
   r->items[phase] = (uint32_t)items.size();
   r->backlog = std::move(items);
   r->backlog_pos = 0;
-  publish_some(sv, r);
+}
+
+// Per-request phase timestamps (milliseconds since submission) appended as a
+// JSON line to the file named by NLOS_SERVE_TRACE, if set.
+void trace_request(Server& sv, Request* r) {
+  if (!sv.trace) return;
+  auto ms = [&](Clock::time_point t) {
+    return t.time_since_epoch().count() == 0
+               ? -1.0
+               : std::chrono::duration<double, std::milli>(t - r->t_submit).count();
+  };
+  std::fprintf(sv.trace,
+               "{\"ticket\": %llu, \"S\": %llu, \"B\": %u, \"P\": %llu, \"items\": %u, "
+               "\"status\": %d, \"admit\": %.3f, \"uploaded\": %.3f, \"prep\": %.3f, "
+               "\"forward\": %.3f, \"reduce\": %.3f, \"noise\": %.3f, \"done\": %.3f}\n",
+               (unsigned long long)r->ticket, (unsigned long long)r->g.S, r->g.B,
+               (unsigned long long)r->g.P, r->items_total, (int)r->status, ms(r->t_mark[0]),
+               ms(r->t_mark[1]), ms(r->t_mark[2]), ms(r->t_mark[3]), ms(r->t_mark[4]),
+               ms(r->t_mark[5]), ms(r->t_done));
+  std::fflush(sv.trace);
 }
 
 void finish(Server& sv, Request* r, nlos_status st, const std::string& msg) {
@@ -541,7 +595,6 @@ void free_request_memory(Server& sv, Request* r) {
 void destroy_request(Server& sv, Request* r) {
   free_request_memory(sv, r);
   if (r->ev) cudaEventDestroy(r->ev);
-  if (r->h_scratch) cudaFreeHost(r->h_scratch);
   sv.reqs.erase(r->ticket);
   delete r;
 }
@@ -575,6 +628,7 @@ bool step(Server& sv) {
     carve(r);
     r->slot = sv.free_slots.back();
     sv.free_slots.pop_back();
+    r->h_scratch = sv.h_scratch + r->slot;
     std::memset(&sv.status[r->slot], 0, sizeof(JobStatus));
     // uploads on the copy stream (copy engines only: the serving kernel may be
     // occupying every SM)
@@ -593,6 +647,7 @@ bool step(Server& sv) {
       continue;
     }
     r->state = R_UPLOAD;
+    r->t_mark[0] = Clock::now();
     sv.active.push_back(r);
     busy = true;
   }
@@ -608,18 +663,20 @@ bool step(Server& sv) {
         fill_job(sv, r, sv.jobs[r->slot]);
         std::atomic_thread_fence(std::memory_order_seq_cst);
         r->state = R_RUNNING;
+        r->t_mark[1] = Clock::now();
         publish_phase(sv, r, PH_PREP);
         busy = true;
       }
     } else if (r->state == R_RUNNING) {
-      if (!r->backlog.empty()) {
-        publish_some(sv, r);
-        busy = true;
-      }
+      if (!r->backlog.empty()) busy = true;
       if (sv.withheld_req == r && (dev_err & kErrWaitTimeout)) {
         // the device gave up on the withheld item: the request cannot finish;
         // its memory stays until every other item published for it is done
+        // (items not yet published never will be)
         sv.withheld_req = nullptr;
+        r->withheld += (uint32_t)(r->backlog.size() - r->backlog_pos);
+        r->backlog.clear();
+        r->backlog_pos = 0;
         r->state = R_DRAINING;
         r->status = NLOS_ETIMEOUT;
         r->msg = "a work item was never published; the device wait gave up";
@@ -627,6 +684,8 @@ bool step(Server& sv) {
       } else {
         const uint32_t done = __atomic_load_n(&sv.status[r->slot].done[r->phase], __ATOMIC_ACQUIRE);
         if (done >= r->items[r->phase]) {
+          r->t_mark[2 + r->phase] = Clock::now();
+          r->items_total += r->items[r->phase];
           int next = r->phase + 1;
           if (next == PH_NOISE && r->g.noise_mode == NLOS_NOISE_NONE) next = 4;
           if (next <= PH_NOISE) {
@@ -665,6 +724,7 @@ bool step(Server& sv) {
         s.noise_scale = r->counts ? h.scale : 0.0;
         s.noise_dark = r->counts ? h.dark : 0.0;
         s.device_error = h.err;
+        s.pairs_full = h.pairs_full;
         if (h.err & kErrBadPoint) finish(sv, r, NLOS_EINVAL, "invalid surface point");
         else if (h.err & kErrWaitTimeout) finish(sv, r, NLOS_ETIMEOUT, "a bounded device wait gave up");
         else finish(sv, r, NLOS_OK, "");
@@ -672,6 +732,7 @@ bool step(Server& sv) {
       }
     }
     if (leave) {
+      trace_request(sv, r);
       sv.active.erase(sv.active.begin() + i);
       if (r->status != NLOS_OK) free_request_memory(sv, r);
       if (r->release_on_done) destroy_request(sv, r);
@@ -680,6 +741,7 @@ bool step(Server& sv) {
       ++i;
     }
   }
+  publish_window(sv);
   // kernel lifecycle: run while items are outstanding, park when idle
   const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
   if (sv.kernel_running && cudaEventQuery(sv.kernel_done) == cudaSuccess) sv.kernel_running = false;
@@ -736,6 +798,7 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
     if (sv.ring) cudaFreeHost(sv.ring);
     if (sv.jobs) cudaFreeHost(sv.jobs);
     if (sv.status) cudaFreeHost(sv.status);
+    if (sv.h_scratch) cudaFreeHost(sv.h_scratch);
     if (sv.d_head) cudaFree(sv.d_head);
     delete s;
     return cuda_error(e, what);
@@ -748,6 +811,8 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
   if ((e = cudaHostAlloc(&sv.ring, sizeof(WorkItem) * kRing, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
   if ((e = cudaHostAlloc(&sv.jobs, sizeof(JobDesc) * kMaxJobs, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
   if ((e = cudaHostAlloc(&sv.status, sizeof(JobStatus) * kMaxJobs, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
+  if ((e = cudaHostAlloc(&sv.h_scratch, sizeof(SceneScratch) * kMaxJobs, cudaHostAllocPortable)) != cudaSuccess)
+    return fail(e, "cudaHostAlloc");
   std::memset(sv.ctl, 0, sizeof(Control));
   std::memset(sv.ring, 0xff, sizeof(WorkItem) * kRing);  // seq = ~0: unpublished
   std::memset(sv.jobs, 0, sizeof(JobDesc) * kMaxJobs);
@@ -768,6 +833,8 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
     return fail(e, "cudaFuncSetAttribute");
   cudaDeviceSynchronize();
   for (int i = kMaxJobs - 1; i >= 0; --i) sv.free_slots.push_back(i);
+  sv.window = std::min<uint64_t>(kWindowPerSm * (uint64_t)sv.num_sms, kRing / 2);
+  if (const char* tp = std::getenv("NLOS_SERVE_TRACE")) sv.trace = std::fopen(tp, "a");
   sv.th = std::thread(run, &sv);
   *out = s;
   return NLOS_OK;
@@ -796,11 +863,9 @@ nlos_status nlos_serve_submit(nlos_server* server, const nlos_params* params,
     delete r;
     return set_error(NLOS_ENOMEM, "host allocation failed");
   }
-  if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaHostAlloc(&r->h_scratch, sizeof(SceneScratch), cudaHostAllocDefault) != cudaSuccess) {
-    if (r->ev) cudaEventDestroy(r->ev);
+  if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
     delete r;
-    return set_error(NLOS_ECUDA, "event or pinned allocation failed");
+    return set_error(NLOS_ECUDA, "event creation failed");
   }
   Server& sv = server->sv;
   {
@@ -895,6 +960,8 @@ nlos_status nlos_server_destroy(nlos_server* server) {
   cudaFreeHost(sv.ring);
   cudaFreeHost(sv.jobs);
   cudaFreeHost(sv.status);
+  cudaFreeHost(sv.h_scratch);
+  if (sv.trace) std::fclose(sv.trace);
   delete server;
   return NLOS_OK;
 }

@@ -20,7 +20,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libnlos.so")
+# the in-tree build; NLOS_LIBRARY may name another build of the same sources
+LIB_PATH = os.environ.get("NLOS_LIBRARY") or os.path.join(_HERE, "libnlos.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ECANCELLED, ENOTFOUND = range(8)
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY",
@@ -67,6 +68,7 @@ class Stats(ctypes.Structure):
         ("noise_dark", ctypes.c_double), ("mean", ctypes.c_double),
         ("variance", ctypes.c_double), ("boundary_pairs", ctypes.c_uint64),
         ("device_error", ctypes.c_uint32),
+        ("pairs_full", ctypes.c_uint64),
     ]
 
     def to_dict(self) -> dict:

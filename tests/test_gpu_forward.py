@@ -218,3 +218,20 @@ def test_paper_dataset_shape():
         H.check_energy(g["energy"][s:s + 1], o["tau_g"].sum(axis=1), allow=allow_e,
                        what=f"energy s={s}")
     print("paper dataset shape: worst rel bin err", worst)
+
+
+def test_early_out_count():
+    """The forward skips (warp, point pair) groups that no lane can bin and
+    reports the pairs it evaluated in full: a multiple of 64, within the padded
+    pair count, and zero when the window lies beyond every path."""
+    params, pts = scenes.workload_union64()
+    g = H.gpu_forward(params, pts, stats=True)
+    full = g["stats"]["pairs_full"]
+    S, P = g["tau"].shape[0], pts.shape[0]
+    assert full % 64 == 0
+    assert 0 < full <= ((S + 31) // 32 * 32) * ((P + 1) // 2 * 2)
+    print("union64 pairs evaluated in full:", full / (S * P))
+    far = dict(params, window_start_m=100.0)
+    g2 = H.gpu_forward(far, pts, stats=True)
+    assert g2["stats"]["pairs_full"] == 0
+    assert not g2["tau"].any()

@@ -94,7 +94,10 @@ def test_served_in_a_mix_equals_alone():
         B = prm["num_bins"]
         tau = _fetch(tau_ptr, (S, B), torch.float32)
         a_tau, a_cnt, a_st = _alone(prm, pts)
-        H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=1e-5,
+        # the server may split the bins into windows (at most 1024 each) where
+        # the standalone launch uses one: window-relative FP32 bin coordinates
+        # round differently, so compare at the per-bin parity bar (1e-4 of peak)
+        H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=H.REL_BIN,
                      what=f"served vs alone ({prm['scan_nx']}x{prm['scan_ny']}x{B})")
         if a_cnt is not None:
             cnt = _fetch(cnt_ptr, (S, B), torch.int32).view(np.uint32)
@@ -183,6 +186,6 @@ def test_withheld_publication_times_out_and_server_recovers():
     S, B = prm["scan_nx"] * prm["scan_ny"], prm["num_bins"]
     tau = _fetch(tau_ptr, (S, B), torch.float32)
     a_tau, _, _ = _alone(prm, pts)
-    H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=1e-5, what="after fault")
+    H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=H.REL_BIN, what="after fault")
     srv.release(t2)
     srv.destroy()

@@ -12,20 +12,23 @@ from tests import gpu_helpers as H
 pytestmark = pytest.mark.gpu
 
 
-def _small(n_side=64, scan=16, seed=0, **kw):
+def _small(n_side=64, scan=16, seed=0, fwhm=60e-12, **kw):
     rng = np.random.default_rng(seed)
     params = scenes.default_params(scan_nx=scan, scan_ny=scan, wall_half_x=0.5, wall_half_y=0.5,
-                                   bin_width_s=8e-12, num_bins=512, jitter_fwhm_s=60e-12,
+                                   bin_width_s=8e-12, num_bins=512, jitter_fwhm_s=fwhm,
                                    bin_mode="splat", **kw)
     pts = scenes.plane_grid(n_side, 0.5, 0.5, scenes.glyph(rng, 8, n_side // 8))
     pts[:, 2] += rng.normal(0, 0.01, size=pts.shape[0]).astype(np.float32)
     return params, pts
 
 
+# 60 ps FWHM at 8 ps bins is sigma = 3.2 bins (moment form), 30 ps is 1.6 bins
+# (per-tap form)
+@pytest.mark.parametrize("fwhm", [60e-12, 30e-12])
 @pytest.mark.parametrize("scan_mode,cos_mode", [("confocal", "object"), ("confocal", "none"),
                                                 ("nonconfocal", "object_wall")])
-def test_splat_forward_matches_oracle(scan_mode, cos_mode):
-    params, pts = _small(scan_mode=scan_mode, cos_mode=cos_mode, laser_xy=(0.1, 0.05))
+def test_splat_forward_matches_oracle(scan_mode, cos_mode, fwhm):
+    params, pts = _small(scan_mode=scan_mode, cos_mode=cos_mode, laser_xy=(0.1, 0.05), fwhm=fwhm)
     g = H.gpu_forward(params, pts)
     o = oracle.forward_splat(params, pts)
     err = H.check_bins(g["tau"], o, what="splat")
@@ -56,12 +59,14 @@ def _grad_compare(params, pts, seed=0):
     return res
 
 
+@pytest.mark.parametrize("fwhm", [60e-12, 30e-12])
 @pytest.mark.parametrize("scan_mode,cos_mode", [("confocal", "object"), ("confocal", "none"),
                                                 ("nonconfocal", "object"),
                                                 ("nonconfocal", "object_wall")])
-def test_adjoint_matches_oracle_gradient(scan_mode, cos_mode):
+def test_adjoint_matches_oracle_gradient(scan_mode, cos_mode, fwhm):
     params, pts = _small(n_side=32, scan=12, scan_mode=scan_mode, cos_mode=cos_mode,
-                         laser_xy=(0.1, 0.05), standoff_m=0.3, standoff_mode="euclidean")
+                         laser_xy=(0.1, 0.05), standoff_m=0.3, standoff_mode="euclidean",
+                         fwhm=fwhm)
     print(scan_mode, cos_mode, _grad_compare(params, pts))
 
 
