@@ -133,6 +133,11 @@ typedef struct {
                                  points at a time, pairs that no lane can bin
                                  (outside the window or facing away), after
                                  computing only r^2 and the cosine numerator */
+  uint64_t pairs_tested;      /* pairs of the (scan tile, point block) units
+                                 the forward evaluated at all; the others were
+                                 ruled out from the bounds of the tile's spots
+                                 and of the block's points without touching
+                                 the pairs (counted per unit: 32 x 1024) */
 } nlos_stats;
 
 typedef struct nlos_scene nlos_scene;
@@ -285,6 +290,13 @@ nlos_status nlos_server_destroy(nlos_server* server);
  * pending and admitted requests (each output nullable). */
 nlos_status nlos_server_stats(nlos_server* server, uint64_t* resident_bytes, uint32_t* pending,
                               uint32_t* active);
+
+/* Device time of the serving kernel so far, in SM clock cycles summed over
+ * its CTAs (one CTA per SM), updated as its launches end: [0] waiting for or
+ * claiming work items, [1] running FORWARD items, [2] running the other
+ * items (pack, zero, reduce, noise). For tuning and monitoring; the paper has
+ * no counterpart. */
+nlos_status nlos_server_device_cycles(nlos_server* server, uint64_t cycles_out[3]);
 
 /* Testing of failure handling, host side only: arms one fault for the next
  * request the scheduler handles. 1 = withhold the publication of its first

@@ -199,6 +199,7 @@ nlos_status nlos_simulate(nlos_scene* scene, float* tau_dev, uint32_t* counts_de
     stats->boundary_pairs = h.boundary_pairs;
     stats->device_error = h.err;
     stats->pairs_full = h.pairs_full;
+    stats->pairs_tested = h.pairs_tested;
     if (h.err & kErrWaitTimeout) return set_error(NLOS_ETIMEOUT, "a bounded device wait gave up");
     if (h.err & kErrBadPoint) return set_error(NLOS_EINVAL, "invalid surface point (see nlos_scene_check)");
   }

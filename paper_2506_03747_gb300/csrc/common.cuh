@@ -5,12 +5,14 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "nlos.h"
 
 namespace nlos {
 
 constexpr double kLightSpeed = 299792458.0;
+constexpr int kTile = 32;  // scan points per forward tile (one per lane)
 
 // ---------------------------------------------------------------------------
 // Error reporting (thread-local message behind nlos_last_error()).
@@ -52,6 +54,33 @@ struct __align__(16) ScanPoint {
   float sx, sy, off, pad;
 };
 
+// Bounds of one sub-block of kSubPairs packed pairs (2 * kSubPairs points,
+// in packed order), for the forward's unit culling:
+//   x/y/z  box of the positions [m], n* box of the unit normals,
+//   uo     range of the point's own path-bin offset (laser leg of a
+//          non-confocal scan, in bins; 0 for confocal),
+//   live   1 if some point can carry weight (albedo * area > 0 and, for a
+//          non-confocal scan with object cosines, facing the laser), else 0.
+constexpr uint32_t kSubPairs = 256;
+struct __align__(16) BlockBound {
+  float x0, x1, y0, y1, z0, z1;
+  float nx0, nx1, ny0, ny1, nz0, nz1;
+  float uo0, uo1, live, pad;
+};
+static_assert(sizeof(BlockBound) == 64, "BlockBound layout");
+
+// Bounds of the scan spots of one tile of kTile scan points (valid ones):
+// spot box and range of the bin offsets off_s.
+struct __align__(16) TileBound {
+  float sx0, sx1, sy0, sy1, off0, off1, pad0, pad1;
+};
+static_assert(sizeof(TileBound) == 32, "TileBound layout");
+
+// Spatial order of the surface points: a counting sort by a 32^3 Morton cell
+// of the scene's bounding box, so that a packed block holds nearby points
+// and its bounds are tight.
+constexpr uint32_t kOrderCells = 32768;
+
 // Device scratch owned by a scene (one per scene). The error word is sticky
 // (cleared by nlos_scene_check); the rest is reset by every forward pass.
 struct SceneScratch {
@@ -66,10 +95,12 @@ struct SceneScratch {
   float scale;                // noise scale (computed on the device)
   float dark;
   unsigned long long pairs_full;  // pairs through the full evaluation (past the early out)
+  unsigned long long next_chunk;  // forward: next chunk of work units to claim
+  unsigned long long pairs_tested;  // pairs of the units the forward staged
   unsigned long long pad3;
 };
 constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
-static_assert(sizeof(SceneScratch) == 64, "scratch layout");
+static_assert(sizeof(SceneScratch) == 80, "scratch layout");
 
 struct Geometry {
   // host-side resolved parameters
@@ -112,16 +143,29 @@ cudaError_t launch_philox(const uint32_t* ctr, uint64_t n, uint32_t k0, uint32_t
 struct SceneImpl {
   nlos_params params;
   Geometry g;
-  PointPair* pairs = nullptr;      // [ceil(P/2)]
+  PointPair* pairs = nullptr;      // [ceil(P/2)] in spatial order
   ScanPoint* scan = nullptr;       // [S padded to the scan tile]
   SceneScratch* scratch = nullptr; // device
   float* raw_points = nullptr;     // [P][8] original records (for the adjoint)
+  uint32_t* perm = nullptr;        // [P] packed position -> original point index
+  uint16_t* cell = nullptr;        // [P] Morton cell of each point (ordering scratch)
+  uint32_t* cells = nullptr;       // [kOrderCells + 8] counts/cursors + box (ordering scratch)
+  BlockBound* bounds = nullptr;    // [ceil(P / 2 / kSubPairs)]
+  TileBound* tiles = nullptr;      // [ceil(S / kTile)]
   cudaStream_t stream = nullptr;   // creation stream
   int device = 0;
   int num_sms = 0;
 };
 
 int jitter_radius(double sigma);
+
+// Spatial ordering, packing and block bounds of a scene's points (order.cu):
+// the device counting sort, then the pack and bounds kernels, on stream st.
+cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st);
+// The same ordering on the host (serving uploads): out[P][8] = pts in order.
+void order_points_host(const float* pts, uint64_t P, float* out);
+// Tile bounds from a scan table (host).
+void tile_bounds_host(const ScanPoint* sp, uint64_t S, std::vector<TileBound>& out);
 
 }  // namespace nlos
 

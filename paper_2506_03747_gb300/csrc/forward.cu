@@ -18,12 +18,14 @@
 //    window) changes. The jitter convolution is linear, so it is applied to
 //    each partial histogram during the flush.
 #include "forward_core.cuh"
+#include "pack_core.cuh"
 
 #include <algorithm>
 
 namespace nlos {
 
-// Standalone launch: the units of one job split evenly over a persistent grid.
+// Standalone launch: a persistent grid (one CTA per SM) claims chunks of the
+// job's work units from a counter in the scene scratch.
 template <int SCAN, int COS, int MODE>
 __global__ void __launch_bounds__(1024, 1)
     fwd_kernel(const __grid_constant__ FwdArgs a, const __grid_constant__ MomTab mt) {
@@ -34,9 +36,7 @@ __global__ void __launch_bounds__(1024, 1)
   sm.hist = reinterpret_cast<float*>(smem);
   sm.stage = reinterpret_cast<PointPair*>(smem + hist_bytes);
   sm.bars = reinterpret_cast<uint64_t*>(sm.stage + (size_t)a.stages * a.ppb);
-  const unsigned long long u0 = (unsigned long long)blockIdx.x * a.units / gridDim.x;
-  const unsigned long long u1 = (unsigned long long)(blockIdx.x + 1) * a.units / gridDim.x;
-  if (u0 >= u1) return;
+  sm.units = reinterpret_cast<unsigned long long*>(sm.bars + 2 * a.stages);
   if (threadIdx.x == 0) {
     for (uint32_t i = 0; i < a.stages; ++i) {
       mbar_init(&sm.bars[i], 1);                                 // full
@@ -46,34 +46,38 @@ __global__ void __launch_bounds__(1024, 1)
   }
   __syncthreads();
   FwdCount cnt;
-#if NLOS_FWD_WS
-  fwd_run_ws<SCAN, COS, MODE>(a, u0, u1, sm, (int)a.stages, cnt, &mt);
-#else
-  if (MODE == MODE_SPLAT_MOM) {
-    fwd_run_ws<SCAN, COS, MODE>(a, u0, u1, sm, (int)a.stages, cnt, &mt);
-  } else {
-    uint32_t it = 0;
-    fwd_run<SCAN, COS, MODE>(a, u0, u1, sm, it, cnt);
-  }
-#endif
+  uint32_t it = 0;
+  (void)fwd_run_ws<SCAN, COS, MODE>(a, 0, 0, sm, (int)a.stages, cnt, &mt, it, a.next_chunk,
+                                    a.chunk, a.units);
   if (MODE == MODE_NEAREST_COUNT && cnt.boundary) atomicAdd(a.boundary, cnt.boundary);
   // the count is warp-uniform: one lane adds it, 64 pairs per warp iteration
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
+  if ((threadIdx.x & 31) == 0 && cnt.tested) atomicAdd(a.pairs_tested, cnt.tested * 64ull);
 }
 
-// Per-pair table (debug/parity): the same pair_eval2 on pair k for scan point
-// s_begin + i; u relative to bin 0, w as accumulated.
+// Per-pair table (debug/parity): the same pack and pair_eval2 arithmetic on
+// the points 2k, 2k + 1 of the caller's order (the forward packs them in a
+// spatial order) for scan point s_begin + i; u relative to bin 0, w as
+// accumulated.
+struct PairTableArgs {
+  const float* raw;
+  unsigned int* err;
+  uint32_t n_pairs, P;
+  int scan_mode, cos_mode;
+  double lx, ly, inv_cdt;
+};
+
 template <int SCAN, int COS>
-__global__ void pair_table_kernel(const PointPair* pairs, uint32_t n_pairs, uint32_t P,
-                                  const ScanPoint* scan, uint64_t s_begin, uint64_t s_count,
-                                  float kbin, float* u_out, float* w_out) {
+__global__ void pair_table_kernel(const PairTableArgs t, const ScanPoint* scan, uint64_t s_begin,
+                                  uint64_t s_count, float kbin, float* u_out, float* w_out) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n_pairs = t.n_pairs, P = t.P;
   if (idx >= s_count * n_pairs) return;
   const uint64_t i = idx / n_pairs;
   const uint32_t k = (uint32_t)(idx % n_pairs);
   const ScanPoint sp = scan[s_begin + i];
-  PointPair q;
-  load_pair(pairs + k, q);
+  const PointPair q = pack_pair_value(t.raw, P, k, t.scan_mode, t.cos_mode, t.lx, t.ly, t.inv_cdt,
+                                      t.err, nullptr);
   float2 u, w, cn;
   pair_eval2<SCAN, COS>(q, make_float2(-sp.sx, -sp.sx), make_float2(-sp.sy, -sp.sy),
                         make_float2(sp.off, sp.off), make_float2(kbin, kbin), u, w, cn);
@@ -158,6 +162,10 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   a.err = &sc.scratch->err;
   a.boundary = &sc.scratch->boundary_pairs;
   a.pairs_full = &sc.scratch->pairs_full;
+  a.pairs_tested = &sc.scratch->pairs_tested;
+  a.bounds = sc.bounds;
+  a.tiles = sc.tiles;
+  a.next_chunk = &sc.scratch->next_chunk;
   a.n_pairs = (uint32_t)((g.P + 1) / 2);
   a.S = (uint32_t)g.S;
   a.B = g.B;
@@ -189,7 +197,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   // pairs per staged block: NLOS_FWD_PPB, halved while the histogram of a
   // full window (up to 1024 bins) would not fit beside the two stages
   a.ppb = NLOS_FWD_PPB;
-  a.stages = NLOS_FWD_WS ? NLOS_FWD_STAGES : 2;
+  a.stages = NLOS_FWD_STAGES;
   while (a.ppb > 256 && (size_t)std::min(g.B, 1024u) * kTile * 4 +
                                 a.stages * (size_t)a.ppb * sizeof(PointPair) + 256 >
                             (size_t)optin)
@@ -198,7 +206,8 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
     a.ppb = kPairsPerBlock;
     a.stages = 2;
   }
-  const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 16 * a.stages + 64;
+  // staged blocks, then full + empty barriers and the unit number of each slot
+  const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 24 * a.stages + 64;
   size_t smem;
   if (moments) {
     // window rows plus 2J halo rows fit the kMomRows moment histograms
@@ -235,6 +244,9 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   unsigned long long grid = (unsigned long long)sc.num_sms * per_sm;
   if (grid > a.units) grid = a.units;
+  // about 8 chunks per CTA on average: fine enough to even out units whose
+  // cost differs (the early out), coarse enough to keep flushes rare
+  a.chunk = std::max<unsigned long long>(1, a.units / (grid * NLOS_FWD_CHUNKS_PER_CTA));
   fn<<<(unsigned)grid, threads, smem, st>>>(a, mt);
   return cudaGetLastError();
 }
@@ -247,10 +259,10 @@ cudaError_t launch_pair_table(const SceneImpl& sc, uint64_t s_begin, uint64_t s_
   if (total == 0) return cudaSuccess;
   const float kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
   const unsigned blocks = (unsigned)((total + 255) / 256);
-  const PointPair* pp = sc.pairs;
-#define NLOS_PT(SC, CO)                                                                    \
-  pair_table_kernel<SC, CO><<<blocks, 256, 0, st>>>(pp, n_pairs, (uint32_t)g.P, sc.scan, \
-                                                    s_begin, s_count, kbin, u, w)
+  PairTableArgs t{sc.raw_points, &sc.scratch->err, n_pairs, (uint32_t)g.P, g.scan_mode,
+                  g.cos_mode, sc.params.laser_x, sc.params.laser_y, 1.0 / g.cdt};
+#define NLOS_PT(SC, CO) \
+  pair_table_kernel<SC, CO><<<blocks, 256, 0, st>>>(t, sc.scan, s_begin, s_count, kbin, u, w)
   if (g.scan_mode == NLOS_CONFOCAL) {
     if (g.cos_mode == NLOS_COS_NONE) NLOS_PT(NLOS_CONFOCAL, NLOS_COS_NONE);
     else if (g.cos_mode == NLOS_COS_OBJECT) NLOS_PT(NLOS_CONFOCAL, NLOS_COS_OBJECT);

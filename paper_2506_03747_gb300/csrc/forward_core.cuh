@@ -28,7 +28,6 @@
 
 namespace nlos {
 
-constexpr int kTile = 32;                   // scan points per CTA tile
 constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23: floor via round-down add
 constexpr int kMagicBits = 0x4B400000;      // bit pattern of kMagic
 constexpr int kMaxTaps = 129;               // fused jitter: R <= 64
@@ -39,17 +38,20 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #ifndef NLOS_FWD_ONE_CTA
 #define NLOS_FWD_ONE_CTA 1                  // standalone forward: 1 CTA x 1024 threads per SM
 #endif
-#ifndef NLOS_FWD_WS
-#define NLOS_FWD_WS 1                       // standalone forward: warp-specialised staging
-#endif
 #ifndef NLOS_FWD_SQRT_RCP
 #define NLOS_FWD_SQRT_RCP 1                 // r from sqrt.approx, weights from one rcp.approx
 #endif
+#ifndef NLOS_FWD_CULL
+#define NLOS_FWD_CULL 1                     // skip (tile, block) units the bounds rule out
+#endif
 #ifndef NLOS_FWD_EARLY
-#define NLOS_FWD_EARLY 1                    // warp-uniform early out before the square roots
+#define NLOS_FWD_EARLY 0                    // warp-uniform early out before the square roots
 #endif
 #ifndef NLOS_FWD_VOTE
 #define NLOS_FWD_VOTE 0                     // 2: warp-uniform skip before the reductions
+#endif
+#ifndef NLOS_FWD_CHUNKS_PER_CTA
+#define NLOS_FWD_CHUNKS_PER_CTA 16          // standalone forward: claimed chunks per CTA (mean)
 #endif
 #ifndef NLOS_FWD_STAGES
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
@@ -87,6 +89,7 @@ inline bool use_moments(double sigma) {
 struct FwdCount {
   unsigned long long boundary = 0;  // pairs within eps of a bin edge (count mode)
   unsigned long long full = 0;      // warp iterations past the early out (x 64 pairs)
+  unsigned long long tested = 0;    // warp iterations of staged units (x 64 pairs)
 };
 
 struct FwdArgs {
@@ -96,7 +99,12 @@ struct FwdArgs {
   unsigned int* err;
   unsigned long long* boundary;
   unsigned long long* pairs_full;  // pairs past the early out (scene scratch)
+  unsigned long long* pairs_tested;  // pairs of staged units (scene scratch)
+  const BlockBound* bounds;   // [ceil(n_pairs / kSubPairs)] or null (no unit culling)
+  const TileBound* tiles;     // [ceil(S / kTile)]
+  unsigned long long* next_chunk;  // standalone launch: chunk counter (zeroed per pass)
   unsigned long long units;   // standalone launch: total units
+  unsigned long long chunk;   // standalone launch: units per claimed chunk
   uint32_t n_pairs, S, B, bw, n_win, n_blk, ppb;
   uint32_t stages;   // staged point blocks (standalone warp-specialised kernel)
   float kbin;        // bins per metre of the scanned leg
@@ -134,15 +142,18 @@ __device__ __forceinline__ void pair_geom2(const PointPair& q, float2 nsx, float
   cn = __ffma2_rn(q.nb, dy, cn);
 }
 
+// u is formed relative to bin 0 of the transient and then moved to the
+// window (nw0 = -w0: an exact subtraction of an integer below 2^24), so the
+// bins and splat taps of a pair do not depend on how the bins are windowed.
 template <int SCAN, int COS>
 __device__ __forceinline__ void pair_finish2(const PointPair& q, float2 r2, float2 cn, float2 off,
-                                             float2 kbin, float2& u, float2& w) {
+                                             float2 kbin, float2 nw0, float2& u, float2& w) {
   const float2 o = (SCAN == NLOS_CONFOCAL) ? off : __fadd2_rn(off, q.uoff);
 #if NLOS_FWD_SQRT_RCP
   // r from the hardware square root; the weight's inverse powers of r from a
   // single reciprocal of r^2k, so no approximation error is raised to a power
   const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
-  u = __ffma2_rn(r, kbin, o);
+  u = __fadd2_rn(__ffma2_rn(r, kbin, o), nw0);
   if (SCAN == NLOS_CONFOCAL) {
     if (COS == NLOS_COS_NONE) {
       const float2 d = __fmul2_rn(r2, r2);
@@ -174,7 +185,7 @@ __device__ __forceinline__ void pair_finish2(const PointPair& q, float2 r2, floa
   const float2 e = __ffma2_rn(make_float2(-r.x, -r.y), ri, make_float2(1.0f, 1.0f));
   ri = __ffma2_rn(__fmul2_rn(ri, make_float2(0.5f, 0.5f)), e, ri);
   r = __fmul2_rn(r2, ri);
-  u = __ffma2_rn(r, kbin, o);
+  u = __fadd2_rn(__ffma2_rn(r, kbin, o), nw0);
   float2 ri2 = __fmul2_rn(ri, ri);
   if (SCAN == NLOS_CONFOCAL) {
     if (COS == NLOS_COS_NONE) {
@@ -203,7 +214,7 @@ __device__ __forceinline__ void pair_eval2(const PointPair& q, float2 nsx, float
                                            float2 kbin, float2& u, float2& w, float2& cn) {
   float2 r2;
   pair_geom2(q, nsx, nsy, r2, cn);
-  pair_finish2<SCAN, COS>(q, r2, cn, off, kbin, u, w);
+  pair_finish2<SCAN, COS>(q, r2, cn, off, kbin, make_float2(0.f, 0.f), u, w);
 }
 
 // Early-out test on r^2, before any square root: can the point land in
@@ -275,10 +286,13 @@ __device__ __forceinline__ void splat_one(uint32_t col_addr, float u, float w, i
 }
 
 struct FwdSmem {
-  float* hist;        // [bw][32]
-  PointPair* stage;   // [stages][ppb]
-  uint64_t* bars;     // full[stages] then empty[stages] (initialised by the caller)
+  float* hist;                 // [bw][32]
+  PointPair* stage;            // [stages][ppb]
+  uint64_t* bars;              // full[stages] then empty[stages] (initialised by the caller)
+  unsigned long long* units;   // [stages]: the unit staged in each slot
 };
+
+constexpr unsigned long long kNoUnit = ~0ull;  // end of a run (in FwdSmem::units)
 
 // Scan-point state of the (tile, window) a CTA is working on; lane l of every
 // warp holds scan point l of the tile.
@@ -286,7 +300,9 @@ struct TileState {
   long long tw = -1;
   uint32_t w0 = 0;
   int lim = 0;  // bins of the current window that lie inside [0, B)
-  float2 sx2, sy2, nsx2, nsy2, off2;
+  float2 sx2, sy2, nsx2, nsy2;
+  float2 off2;          // bin offset of the scan point, relative to bin 0
+  float2 nw02;          // -(first bin of the window)
   float2 r2lo2, r2hi2;  // early-out bounds (see may_bin2)
 };
 
@@ -312,8 +328,9 @@ __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int la
     ts.sy2 = make_float2(sp.sy, sp.sy);
     ts.nsx2 = make_float2(-sp.sx, -sp.sx);
     ts.nsy2 = make_float2(-sp.sy, -sp.sy);
+    ts.off2 = make_float2(sp.off, sp.off);
+    ts.nw02 = make_float2(-(float)ts.w0, -(float)ts.w0);
     const float o = sp.off - (float)ts.w0;
-    ts.off2 = make_float2(o, o);
     // r range of u in [-margin, lim + margin): r = (u - o) / kbin
     const float ik = 1.0f / a.kbin;
     const float rlo = (-margin - o) * ik, rhi = ((float)ts.lim + margin - o) * ik;
@@ -330,6 +347,7 @@ __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int la
   } else {
     ts.sx2 = ts.sy2 = ts.nsx2 = ts.nsy2 = make_float2(0.f, 0.f);
     ts.off2 = make_float2(-1e30f, -1e30f);  // u -> -inf: never binned
+    ts.nw02 = make_float2(0.f, 0.f);
     ts.r2lo2 = make_float2(1.f, 1.f);      // empty r ranges
     ts.r2hi2 = make_float2(-1.f, -1.f);
   }
@@ -423,18 +441,21 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
     load_pair(blkp + i, q);
     float2 r2, cn;
     pair_geom2(q, ts.nsx2, ts.nsy2, r2, cn);
+    ++cnt.tested;
 #if NLOS_FWD_EARLY
     // warp-uniform early out: for most (tile, point) combinations of a
-    // scene no lane can bin either point (outside the window or facing away)
-    // (the boundary count takes every pair near a bin edge, facing or not)
-    const bool2_t m = may_bin2<SCAN>(q, r2, ts.r2lo2, ts.r2hi2, ikbin_neg);
-    const bool fa = MODE == MODE_NEAREST_COUNT || facing<COS>(cn.x);
-    const bool fb = MODE == MODE_NEAREST_COUNT || facing<COS>(cn.y);
-    if (!__any_sync(0xffffffffu, (m.x && fa) || (m.y && fb))) continue;
+    // scene no lane can bin either point (outside the window or facing away).
+    // Not in the boundary-count mode, which counts every pair near a bin
+    // edge of the whole transient (facing or not) in the first window's pass.
+    if (MODE != MODE_NEAREST_COUNT) {
+      const bool2_t m = may_bin2<SCAN>(q, r2, ts.r2lo2, ts.r2hi2, ikbin_neg);
+      if (!__any_sync(0xffffffffu, (m.x && facing<COS>(cn.x)) || (m.y && facing<COS>(cn.y))))
+        continue;
+    }
 #endif
     ++cnt.full;
     float2 u, w;
-    pair_finish2<SCAN, COS>(q, r2, cn, ts.off2, kbin2, u, w);
+    pair_finish2<SCAN, COS>(q, r2, cn, ts.off2, kbin2, ts.nw02, u, w);
     if (MODE == MODE_SPLAT) {
       if (facing<COS>(cn.x)) splat_one(col_addr, u.x, w.x, ts.lim, a);
       if (facing<COS>(cn.y)) splat_one(col_addr, u.y, w.y, ts.lim, a);
@@ -558,64 +579,60 @@ __device__ __forceinline__ void issue_block(const FwdArgs& a, const FwdSmem& sm,
   bulk_g2s(sm.stage + (size_t)slot * a.ppb, a.pairs + first, bytes, &sm.bars[slot]);
 }
 
-// Runs the work units [u0, u1) of one job (a contiguous range in (tile,
-// window, point block) order) on this CTA and flushes its partial histograms
-// into a.tau. Two staged blocks, all warps compute, CTA barriers between
-// blocks (used by the serving kernel, whose CTAs switch jobs between calls).
-// The staging use counter `it_base` carries the mbarrier phases across
-// calls. Returns false if a bounded wait gave up (the error is recorded in
-// *a.err); every thread returns the same value.
-template <int SCAN, int COS, int MODE>
-__device__ bool fwd_run(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
-                        const FwdSmem& sm, uint32_t& it_base, FwdCount& cnt) {
-  float* hist = sm.hist;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
-  const int nwarps = blockDim.x >> 5;
-  if (u0 >= u1) return true;
-  if (tid == 0) {
-    issue_block(a, sm, u0, it_base & 1);
-    if (u0 + 1 < u1) issue_block(a, sm, u0 + 1, (it_base + 1) & 1);
+// max of a * b over a in [a0, a1], b in [b0, b1]
+__device__ __forceinline__ float imax(float a0, float a1, float b0, float b1) {
+  return fmaxf(fmaxf(a0 * b0, a0 * b1), fmaxf(a1 * b0, a1 * b1));
+}
+
+// Can unit (tile, window, point block) bin anything? From the block's
+// bounds and the tile's: the range of u over every (spot, point) of the
+// unit (distance bounds between the spot box at z = 0 and the point box)
+// against the window with `margin` bins on each side, the object cosine
+// (upper bound of n.(spot - x) over the boxes) and whether any point carries
+// weight. Conservative: a unit it keeps may still bin nothing.
+template <int SCAN, int COS>
+__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin) {
+  const unsigned long long tw = unit / a.n_blk;
+  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
+  const uint32_t tile = (uint32_t)(tw / a.n_win);
+  const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
+  const float lim = (float)min(a.bw, a.B - w0);
+  const TileBound t = a.tiles[tile];
+  const uint32_t sub_per = a.ppb / kSubPairs;
+  const uint32_t sb0 = blk * sub_per;
+  const uint32_t n_sub = (a.n_pairs + kSubPairs - 1) / kSubPairs;
+  BlockBound b = a.bounds[sb0];
+  for (uint32_t j = 1; j < sub_per && sb0 + j < n_sub; ++j) {
+    const BlockBound c = a.bounds[sb0 + j];
+    b.x0 = fminf(b.x0, c.x0); b.x1 = fmaxf(b.x1, c.x1);
+    b.y0 = fminf(b.y0, c.y0); b.y1 = fmaxf(b.y1, c.y1);
+    b.z0 = fminf(b.z0, c.z0); b.z1 = fmaxf(b.z1, c.z1);
+    b.nx0 = fminf(b.nx0, c.nx0); b.nx1 = fmaxf(b.nx1, c.nx1);
+    b.ny0 = fminf(b.ny0, c.ny0); b.ny1 = fmaxf(b.ny1, c.ny1);
+    b.nz0 = fminf(b.nz0, c.nz0); b.nz1 = fmaxf(b.nz1, c.nz1);
+    b.uo0 = fminf(b.uo0, c.uo0); b.uo1 = fmaxf(b.uo1, c.uo1);
+    b.live = fmaxf(b.live, c.live);
   }
-  const uint32_t col_addr = smem_addr(hist) + (uint32_t)lane * 4u;
-  TileState ts;
-  for (unsigned long long unit = u0; unit < u1; ++unit) {
-    const uint32_t it = it_base + (uint32_t)(unit - u0);
-    const int slot = it & 1;
-    const uint32_t parity = (it >> 1) & 1;
-    const long long tw = (long long)(unit / a.n_blk);
-    const uint32_t blk = (uint32_t)(unit - (unsigned long long)tw * a.n_blk);
-    if (tw != ts.tw) {
-      if (ts.tw >= 0) {
-        flush_tile<MODE>(a, ts.tw, hist, warp, nwarps);
-        __syncthreads();
-      }
-      for (uint32_t i = tid; i < a.bw * kTile; i += blockDim.x) hist[i] = 0.f;
-      load_tile(a, tw, lane, ts, SCAN == NLOS_CONFOCAL, window_margin<MODE>(a, 0));
-      __syncthreads();
-    }
-    const bool ok = mbar_wait_bounded(&sm.bars[slot], parity);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(a.err, kErrWaitTimeout);
-        if (unit + 1 < u1) (void)mbar_wait_bounded(&sm.bars[slot ^ 1], ((it + 1) >> 1) & 1);
-      }
-      it_base += (uint32_t)(u1 - u0);
-      return false;
-    }
-    const uint32_t first = blk * a.ppb;
-    compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb, min(a.ppb, a.n_pairs - first),
-                                   warp, nwarps, ts, col_addr, cnt);
-    __syncthreads();
-    if (tid == 0 && unit + 2 < u1) {
-      fence_proxy_async_smem();
-      issue_block(a, sm, unit + 2, slot);
-    }
+  if (b.live == 0.f) return false;
+  const float dx = fmaxf(0.f, fmaxf(b.x0 - t.sx1, t.sx0 - b.x1));
+  const float dy = fmaxf(0.f, fmaxf(b.y0 - t.sy1, t.sy0 - b.y1));
+  const float rmin = sqrtf(dx * dx + dy * dy + b.z0 * b.z0);
+  const float fx = fmaxf(fabsf(b.x1 - t.sx0), fabsf(t.sx1 - b.x0));
+  const float fy = fmaxf(fabsf(b.y1 - t.sy0), fabsf(t.sy1 - b.y0));
+  const float rmax = sqrtf(fx * fx + fy * fy + b.z1 * b.z1);
+  float ulo = fmaf(rmin, a.kbin, t.off0) - (float)w0;
+  float uhi = fmaf(rmax, a.kbin, t.off1) - (float)w0;
+  if (SCAN != NLOS_CONFOCAL) {
+    ulo += b.uo0;
+    uhi += b.uo1;
   }
-  flush_tile<MODE>(a, ts.tw, hist, warp, nwarps);
-  __syncthreads();  // histogram reads done before the next call zeroes it
-  it_base += (uint32_t)(u1 - u0);
+  if (uhi < -margin || ulo >= lim + margin) return false;
+  if (COS != NLOS_COS_NONE) {
+    const float f = imax(b.nx0, b.nx1, t.sx0 - b.x1, t.sx1 - b.x0) +
+                    imax(b.ny0, b.ny1, t.sy0 - b.y1, t.sy1 - b.y0) +
+                    imax(b.nz0, b.nz1, -b.z1, -b.z0);
+    if (f <= 0.f) return false;
+  }
   return true;
 }
 
@@ -627,23 +644,28 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Warp-specialised variant for the standalone kernel (one job per launch):
-// warp 0 stages point blocks with TMA into `stages` buffers, the other warps
-// compute; a consumer warp releases a buffer by arriving on its "empty"
-// mbarrier, so warps never wait for one another between blocks. CTA-wide
-// synchronisation (a named barrier over the consumer warps) happens only when
-// the (tile, window) changes. Bars: full[0..stages) (count 1 + bytes),
-// empty[stages..2 stages) (count = consumer warps). Every wait is bounded; a
-// wait that gives up sets *a.err and an abort flag, after which the warps skip
-// their work but keep arriving, so no barrier is left waiting.
+// Warp-specialised run of work units (tile, window, point block) of one job:
+// warp 0 (one lane) stages point blocks with TMA bulk copies into `stages`
+// slots, the other warps evaluate them. The producer writes each slot's unit
+// number beside it (kNoUnit ends the run); the full barrier orders that write
+// before the consumers read it. Units come either from the range [u0, u1)
+// (chunk_counter == nullptr) or in chunks of `chunk` units claimed from
+// *chunk_counter until units_total is reached, so that CTAs that meet cheap
+// units (most pairs stopped by the early out) take more of them. Consumers
+// flush their (tile, window) histogram whenever the tile changes and at the
+// end. `it` carries the barrier phases across calls (the serving kernel runs
+// one call per work item). Every wait is bounded; returns false if one gave
+// up (the error is in *a.err).
 template <int SCAN, int COS, int MODE>
-__device__ void fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
-                           const FwdSmem& sm, int stages, FwdCount& cnt,
-                           const MomTab* mt = nullptr) {
+__device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
+                           const FwdSmem& sm, int stages, FwdCount& cnt, const MomTab* mt,
+                           uint32_t& it, unsigned long long* chunk_counter = nullptr,
+                           unsigned long long chunk = 0, unsigned long long units_total = 0) {
   const int mom_J = (MODE == MODE_SPLAT_MOM) ? mt->J : 0;
   const uint32_t hist_words = (MODE == MODE_SPLAT_MOM) ? (uint32_t)kMoments * kMomRows * kTile
                                                        : a.bw * kTile;
   __shared__ int s_abort;
+  __shared__ uint32_t s_used;  // slots this call used (units + the end mark)
   float* hist = sm.hist;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -651,70 +673,140 @@ __device__ void fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
   const int ncw = (blockDim.x >> 5) - 1;  // consumer warps
   uint64_t* full = sm.bars;
   uint64_t* empty = sm.bars + stages;
-  if (tid == 0) s_abort = 0;
+  unsigned long long* unit_of = sm.units;
+  if (tid == 0) {
+    s_abort = 0;
+    s_used = 0;
+  }
   __syncthreads();
-  const uint32_t nunits = (uint32_t)(u1 - u0);
   if (warp == 0) {
+    // The whole warp walks the units 32 at a time: each lane tests one unit
+    // against the bounds (unit_live), then lane 0 stages the live ones in
+    // order. Chunk claims (lane 0) run one ahead of their use.
+    const bool cull = NLOS_FWD_CULL && a.bounds != nullptr && MODE != MODE_NEAREST_COUNT;
+    const float margin = window_margin<MODE>(a, mom_J);
+    unsigned long long cur = u0, lim = u1, next = 0;
+    if (chunk_counter) {
+      unsigned long long c = 0, n2 = 0;
+      if (lane == 0) {
+        c = atomicAdd(chunk_counter, 1ull);
+        n2 = atomicAdd(chunk_counter, 1ull);
+      }
+      c = __shfl_sync(0xffffffffu, c, 0);
+      next = __shfl_sync(0xffffffffu, n2, 0);
+      cur = min(c * chunk, units_total);
+      lim = min(cur + chunk, units_total);
+    }
+    uint32_t k = 0;
+    bool failed = false;
+    for (;;) {
+      if (cur == lim && chunk_counter && cur < units_total) {
+        cur = min(next * chunk, units_total);
+        lim = min(cur + chunk, units_total);
+        if (cur < lim) {
+          unsigned long long n2 = 0;
+          if (lane == 0) n2 = atomicAdd(chunk_counter, 1ull);
+          next = __shfl_sync(0xffffffffu, n2, 0);
+        }
+      }
+      if (cur >= lim) break;
+      const uint32_t n = (uint32_t)min(32ull, lim - cur);
+      const bool live = lane < n && (!cull || unit_live<SCAN, COS>(a, cur + lane, margin));
+      uint32_t mask = __ballot_sync(0xffffffffu, live);
+      if (lane == 0) {
+        while (mask) {
+          const int j = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const uint32_t g = it + k;  // slot uses continue across calls
+          const int slot = (int)(g % (uint32_t)stages);
+          const uint32_t use = g / (uint32_t)stages;
+          if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1)) {
+            atomicOr(a.err, kErrWaitTimeout);
+            s_abort = 1;
+            failed = true;
+            break;
+          }
+          unit_of[slot] = cur + j;
+          fence_proxy_async_smem();
+          issue_block(a, sm, cur + j, slot);
+          ++k;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, (int)failed, 0)) break;
+      cur += n;
+    }
     if (lane == 0) {
-      uint32_t k = 0;
-      for (; k < nunits; ++k) {
-        const int slot = (int)(k % (uint32_t)stages);
-        const uint32_t use = k / (uint32_t)stages;
+      if (!failed) {
+        // end mark: no copy, a plain arrival completes the slot
+        const uint32_t g = it + k;
+        const int slot = (int)(g % (uint32_t)stages);
+        const uint32_t use = g / (uint32_t)stages;
         if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1)) {
           atomicOr(a.err, kErrWaitTimeout);
           s_abort = 1;
-          break;
+        } else {
+          unit_of[slot] = kNoUnit;
+          mbar_arrive(&full[slot]);
+          ++k;
         }
-        fence_proxy_async_smem();
-        issue_block(a, sm, u0 + k, slot);
       }
-      // copies still in flight must land before the CTA can exit: wait for
-      // the last use of every stage that was issued (bounded)
+      // copies still in flight must land before the CTA exits or reuses the
+      // stages: wait for the last use of every slot (bounded)
       for (uint32_t j = (k > (uint32_t)stages ? k - (uint32_t)stages : 0); j < k; ++j)
-        (void)mbar_wait_bounded(&full[j % (uint32_t)stages], (j / (uint32_t)stages) & 1);
+        (void)mbar_wait_bounded(&full[(it + j) % (uint32_t)stages],
+                                ((it + j) / (uint32_t)stages) & 1);
+      s_used = k;
     }
   } else {
     const int cw = warp - 1;
     const int nthr = ncw * 32;
     const uint32_t col_addr = smem_addr(hist) + (uint32_t)lane * 4u;
     TileState ts;
-    for (uint32_t k = 0; k < nunits; ++k) {
-      const unsigned long long unit = u0 + k;
-      const int slot = (int)(k % (uint32_t)stages);
-      const uint32_t use = k / (uint32_t)stages;
-      const long long tw = (long long)(unit / a.n_blk);
-      const uint32_t blk = (uint32_t)(unit - (unsigned long long)tw * a.n_blk);
-      if (tw != ts.tw) {
-        named_barrier(1, nthr);  // every consumer is done with the previous tile
-        if (ts.tw >= 0) {
-          if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
-          else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
-          named_barrier(1, nthr);
-        }
-        for (uint32_t i = tid - 32; i < hist_words; i += nthr) hist[i] = 0.f;
-        load_tile(a, tw, lane, ts, SCAN == NLOS_CONFOCAL, window_margin<MODE>(a, mom_J));
-        named_barrier(1, nthr);
-      }
-      const bool aborted = *(volatile int*)&s_abort != 0;
-      if (!aborted) {
-        if (mbar_wait_bounded(&full[slot], use & 1)) {
-          const uint32_t first = blk * a.ppb;
-          compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb,
-                                         min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
-                                         cnt, mom_J);
-        } else if (lane == 0) {
+    for (uint32_t k = 0;; ++k) {
+      const uint32_t g = it + k;
+      const int slot = (int)(g % (uint32_t)stages);
+      const uint32_t use = g / (uint32_t)stages;
+      if (*(volatile int*)&s_abort != 0) break;
+      if (!mbar_wait_bounded(&full[slot], use & 1)) {
+        if (lane == 0) {
           atomicOr(a.err, kErrWaitTimeout);
           s_abort = 1;
         }
+        break;
+      }
+      const unsigned long long unit = *(volatile unsigned long long*)&unit_of[slot];
+      if (unit != kNoUnit) {
+        const long long tw = (long long)(unit / a.n_blk);
+        const uint32_t blk = (uint32_t)(unit - (unsigned long long)tw * a.n_blk);
+        if (tw != ts.tw) {
+          named_barrier(1, nthr);  // every consumer is done with the previous tile
+          if (ts.tw >= 0) {
+            if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
+            else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+            named_barrier(1, nthr);
+          }
+          for (uint32_t i = tid - 32; i < hist_words; i += nthr) hist[i] = 0.f;
+          load_tile(a, tw, lane, ts, SCAN == NLOS_CONFOCAL, window_margin<MODE>(a, mom_J));
+          named_barrier(1, nthr);
+        }
+        const uint32_t first = blk * a.ppb;
+        compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb,
+                                       min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
+                                       cnt, mom_J);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
+      if (unit == kNoUnit) break;
     }
     named_barrier(1, nthr);
-    if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
-    else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+    if (ts.tw >= 0) {
+      if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
+      else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+    }
   }
   __syncthreads();
+  it += s_used;
+  return s_abort == 0;
 }
 
 }  // namespace nlos

@@ -15,14 +15,17 @@ namespace nlos {
 //                 OBJECT: (na, nb, nc) = -K * (nx, ny, nz z); WALL: K * z / r_l * z;
 //                 NONE: kq = q / r_l^2; uoff = r_l / (c dt).
 // q = albedo * area.
-__device__ __forceinline__ void pack_pair(const float* __restrict__ raw, uint64_t P, uint64_t k,
-                                          int scan_mode, int cos_mode, double lx, double ly,
-                                          double inv_cdt, PointPair* pairs, unsigned int* err) {
+// perm (nullable): packed position -> index of the point in raw.
+__device__ __forceinline__ PointPair pack_pair_value(const float* __restrict__ raw, uint64_t P,
+                                                     uint64_t k, int scan_mode, int cos_mode,
+                                                     double lx, double ly, double inv_cdt,
+                                                     unsigned int* err,
+                                                     const uint32_t* __restrict__ perm) {
   float f[2][8];
   for (int h = 0; h < 2; ++h) {
     const uint64_t i = 2 * k + h;
     if (i < P) {
-      const float* r = raw + 8 * i;
+      const float* r = raw + 8 * (perm ? (uint64_t)perm[i] : i);
       double nn = 0.0;
       bool ok = true;
       for (int c = 0; c < 8; ++c) ok = ok && isfinite(r[c]);
@@ -70,7 +73,64 @@ __device__ __forceinline__ void pack_pair(const float* __restrict__ raw, uint64_
   o.nb = make_float2(f[0][5], f[1][5]);
   o.nc = make_float2(f[0][6], f[1][6]);
   o.uoff = make_float2(f[0][7], f[1][7]);
-  pairs[k] = o;
+  return o;
+}
+
+__device__ __forceinline__ void pack_pair(const float* __restrict__ raw, uint64_t P, uint64_t k,
+                                          int scan_mode, int cos_mode, double lx, double ly,
+                                          double inv_cdt, PointPair* pairs, unsigned int* err,
+                                          const uint32_t* __restrict__ perm = nullptr) {
+  pairs[k] = pack_pair_value(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, err, perm);
+}
+
+// Bounds of sub-block sb (points 2 kSubPairs sb .. in packed order) by one
+// warp; lane 0 writes *out. Same per-point quantities as pack_pair.
+__device__ __forceinline__ void block_bound_warp(const float* __restrict__ raw, uint64_t P,
+                                                 uint64_t sb, int scan_mode, int cos_mode,
+                                                 double lx, double ly, double inv_cdt,
+                                                 const uint32_t* __restrict__ perm,
+                                                 BlockBound* out) {
+  const int lane = threadIdx.x & 31;
+  float lo[7], hi[7];
+  for (int c = 0; c < 7; ++c) {
+    lo[c] = 3.0e38f;
+    hi[c] = -3.0e38f;
+  }
+  float live = 0.f;
+  const uint64_t first = sb * 2 * kSubPairs;
+  const uint64_t last = min(P, first + 2 * kSubPairs);
+  for (uint64_t i = first + lane; i < last; i += 32) {
+    const float* r = raw + 8 * (perm ? (uint64_t)perm[i] : i);
+    const float x = r[0], y = r[1], z = r[2];
+    float uo = 0.f;
+    bool w = r[6] * r[7] > 0.f;
+    if (scan_mode == NLOS_NONCONFOCAL) {
+      const double vx = x - lx, vy = y - ly, vz = z;
+      const double rl = sqrt(vx * vx + vy * vy + vz * vz);
+      uo = (float)(rl * inv_cdt);
+      if (cos_mode != NLOS_COS_NONE) w = w && -(r[3] * vx + r[4] * vy + r[5] * vz) > 0.0;
+    }
+    const float v[7] = {x, y, z, r[3], r[4], r[5], uo};
+    for (int c = 0; c < 7; ++c) {
+      lo[c] = fminf(lo[c], v[c]);
+      hi[c] = fmaxf(hi[c], v[c]);
+    }
+    if (w) live = 1.f;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int c = 0; c < 7; ++c) {
+      lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+      hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+    }
+    live = fmaxf(live, __shfl_xor_sync(0xffffffffu, live, o));
+  }
+  if (lane == 0) {
+    BlockBound b;
+    b.x0 = lo[0]; b.x1 = hi[0]; b.y0 = lo[1]; b.y1 = hi[1]; b.z0 = lo[2]; b.z1 = hi[2];
+    b.nx0 = lo[3]; b.nx1 = hi[3]; b.ny0 = lo[4]; b.ny1 = hi[4]; b.nz0 = lo[5]; b.nz1 = hi[5];
+    b.uo0 = lo[6]; b.uo1 = hi[6]; b.live = live; b.pad = 0.f;
+    *out = b;
+  }
 }
 
 }  // namespace nlos

@@ -79,14 +79,6 @@ nlos_status resolve(const nlos_params& p, uint64_t num_points, Geometry& g) {
   return NLOS_OK;
 }
 
-__global__ void pack_kernel(const float* __restrict__ raw, uint64_t P, int scan_mode, int cos_mode,
-                            double lx, double ly, double inv_cdt, PointPair* pairs,
-                            unsigned int* err) {
-  const uint64_t n_pairs = (P + 1) / 2;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs; k += stride)
-    pack_pair(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, pairs, err);
-}
 
 // Per-scan-point spot and bin offset off_s = (legs(s) - L0) / (c dt), FP64.
 void scan_points(const nlos_params& p, const Geometry& g, std::vector<ScanPoint>& out) {
@@ -139,10 +131,9 @@ nlos_status scene_create(const nlos_params* params, const float* pts, uint64_t P
   s.g = g;
   s.stream = st;
   auto fail = [&](nlos_status code, const std::string& msg) {
-    if (s.pairs) cudaFree(s.pairs);
-    if (s.scan) cudaFree(s.scan);
-    if (s.scratch) cudaFree(s.scratch);
-    if (s.raw_points) cudaFree(s.raw_points);
+    for (void* q : {(void*)s.pairs, (void*)s.scan, (void*)s.scratch, (void*)s.raw_points,
+                    (void*)s.perm, (void*)s.cell, (void*)s.cells, (void*)s.bounds, (void*)s.tiles})
+      if (q) cudaFree(q);
     delete sc;
     return set_error(code, msg);
   };
@@ -151,28 +142,31 @@ nlos_status scene_create(const nlos_params* params, const float* pts, uint64_t P
   if (e != cudaSuccess) return fail(NLOS_ECUDA, cudaGetErrorString(e));
 
   const uint64_t n_pairs = (P + 1) / 2;
+  const uint64_t n_sub = (n_pairs + kSubPairs - 1) / kSubPairs;
   std::vector<ScanPoint> hs;
   scan_points(*params, g, hs);
+  std::vector<TileBound> ht;
+  tile_bounds_host(hs.data(), g.S, ht);
   if ((e = cudaMalloc(&s.scratch, sizeof(SceneScratch))) != cudaSuccess ||
       (e = cudaMalloc(&s.scan, sizeof(ScanPoint) * (g.S ? g.S : 1))) != cudaSuccess ||
+      (e = cudaMalloc(&s.tiles, sizeof(TileBound) * (ht.empty() ? 1 : ht.size()))) != cudaSuccess ||
       (P > 0 && (e = cudaMalloc(&s.pairs, sizeof(PointPair) * n_pairs)) != cudaSuccess) ||
-      (P > 0 && (e = cudaMalloc(&s.raw_points, sizeof(float) * 8 * P)) != cudaSuccess))
+      (P > 0 && (e = cudaMalloc(&s.raw_points, sizeof(float) * 8 * P)) != cudaSuccess) ||
+      (P > 0 && (e = cudaMalloc(&s.perm, sizeof(uint32_t) * P)) != cudaSuccess) ||
+      (P > 0 && (e = cudaMalloc(&s.cell, sizeof(uint16_t) * P)) != cudaSuccess) ||
+      (P > 0 && (e = cudaMalloc(&s.cells, sizeof(uint32_t) * (kOrderCells + 8))) != cudaSuccess) ||
+      (P > 0 && (e = cudaMalloc(&s.bounds, sizeof(BlockBound) * n_sub)) != cudaSuccess))
     return fail(NLOS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
 
   e = cudaMemsetAsync(s.scratch, 0, sizeof(SceneScratch), st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s.scan, hs.data(), sizeof(ScanPoint) * g.S, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !ht.empty())
+    e = cudaMemcpyAsync(s.tiles, ht.data(), sizeof(TileBound) * ht.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && P > 0)
     e = cudaMemcpyAsync(s.raw_points, pts, sizeof(float) * 8 * P,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && P > 0) {
-    const uint64_t want = (n_pairs + 255) / 256;
-    const unsigned blocks = (unsigned)(want < (uint64_t)s.num_sms * 8 ? want : (uint64_t)s.num_sms * 8);
-    pack_kernel<<<blocks, 256, 0, st>>>(s.raw_points, P, g.scan_mode, g.cos_mode,
-                                        params->laser_x, params->laser_y, 1.0 / g.cdt, s.pairs,
-                                        &s.scratch->err);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess && P > 0) e = launch_order_pack(s, st);
   unsigned int err = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&err, &s.scratch->err, sizeof(err), cudaMemcpyDeviceToHost, st);
@@ -195,14 +189,8 @@ nlos_status scene_set_points(nlos_scene* sc, const float* pts, uint64_t P, int o
   cudaError_t e = cudaMemcpyAsync(s.raw_points, pts, sizeof(float) * 8 * P,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(points)");
-  const uint64_t n_pairs = (P + 1) / 2;
-  const uint64_t want = (n_pairs + 255) / 256;
-  const unsigned blocks = (unsigned)(want < (uint64_t)s.num_sms * 8 ? want : (uint64_t)s.num_sms * 8);
-  pack_kernel<<<blocks, 256, 0, st>>>(s.raw_points, P, s.g.scan_mode, s.g.cos_mode,
-                                      s.params.laser_x, s.params.laser_y, 1.0 / s.g.cdt, s.pairs,
-                                      &s.scratch->err);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_error(e, "pack_kernel");
+  e = launch_order_pack(s, st);
+  if (e != cudaSuccess) return cuda_error(e, "order/pack kernels");
   return NLOS_OK;
 }
 
@@ -215,6 +203,8 @@ nlos_status scene_destroy(nlos_scene* sc) {
   if (s.scan && (e2 = cudaFree(s.scan)) != cudaSuccess) e = e2;
   if (s.scratch && (e2 = cudaFree(s.scratch)) != cudaSuccess) e = e2;
   if (s.raw_points && (e2 = cudaFree(s.raw_points)) != cudaSuccess) e = e2;
+  for (void* q : {(void*)s.perm, (void*)s.cell, (void*)s.cells, (void*)s.bounds, (void*)s.tiles})
+    if (q && (e2 = cudaFree(q)) != cudaSuccess) e = e2;
   delete sc;
   if (e != cudaSuccess) return cuda_error(e, "cudaFree");
   return NLOS_OK;

@@ -58,16 +58,31 @@ __host__ __device__ inline int phase_of(uint32_t kind) {
 
 constexpr uint64_t kRing = 1ull << 16;      // work-item ring slots
 constexpr int kMaxJobs = 1024;               // concurrently admitted requests
-constexpr uint32_t kCapBw = 1024;            // histogram bins per window in the serving kernel
-constexpr uint32_t kPackChunk = 16384;       // pairs per PACK item
-constexpr uint64_t kZeroChunk = 1ull << 18;  // floats per ZERO item
-constexpr uint32_t kFwdChunk = 32;           // point blocks per FORWARD item
+#ifndef NLOS_SERVE_FWD_INLINE
+#define NLOS_SERVE_FWD_INLINE __forceinline__
+#endif
+#ifndef NLOS_SERVE_CAPBW
+#define NLOS_SERVE_CAPBW 1024
+#endif
+#ifndef NLOS_SERVE_FWD_CHUNK
+#define NLOS_SERVE_FWD_CHUNK 64
+#endif
+#ifndef NLOS_SERVE_PPB
+#define NLOS_SERVE_PPB 512
+#endif
+constexpr uint32_t kCapBw = NLOS_SERVE_CAPBW;  // histogram bins per window in the serving kernel
+constexpr uint32_t kServePpb = NLOS_SERVE_PPB; // pairs per staged point block
+constexpr uint32_t kPackChunk = 2048;        // pairs per PACK item (a multiple of kSubPairs)
+static_assert(kPackChunk % kSubPairs == 0, "pack items start on sub-block edges");
+constexpr uint64_t kZeroChunk = 1ull << 16;  // floats per ZERO item
+constexpr uint32_t kFwdChunk = NLOS_SERVE_FWD_CHUNK;  // point blocks per FORWARD item
 constexpr uint64_t kWindowPerSm = 16;        // items outstanding per SM (publication window)
 constexpr uint64_t kMaxPhaseItems = 16384;   // FORWARD items per request (coarser beyond)
 constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
-constexpr uint64_t kNoiseChunk = 1ull << 15; // bins per NOISE item
+constexpr uint64_t kNoiseChunk = 1ull << 13; // bins per NOISE item
 constexpr long long kIdleCycles = 2000000000LL;  // ~1 s without work: exit
-constexpr int kServeThreads = 512;            // 16 warps: room for the registers of every fused path
+constexpr int kServeThreads = 1024;           // 1 producer + 31 consumer warps (as the forward)
+constexpr int kServeStages = 3;               // staged point blocks in flight
 constexpr uint64_t kNone = ~0ull;
 constexpr uint64_t kSkip = ~0ull - 1;
 
@@ -102,6 +117,10 @@ struct Control {
   uint32_t err;        // device: kErr* bits
   int32_t alive;       // device: CTAs running
   uint32_t pad[7];
+  // device: SM cycles (summed over CTAs) spent waiting for or claiming work,
+  // running FORWARD items, and running the other items
+  unsigned long long cycles[3];
+  unsigned long long pad2;
 };
 
 struct JobStatus {
@@ -126,32 +145,41 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
-template <int SCAN, int COS>
-__device__ bool fwd_item_mode(const FwdArgs& a, uint64_t b, uint64_t e, const FwdSmem& sm,
-                              uint32_t& it, int bin_mode) {
+// One instance per (scan, cosine, bin mode).
+template <int SCAN, int COS, int MODE>
+__device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, uint64_t b, uint64_t e,
+                                           const FwdSmem& sm, uint32_t& it) {
   FwdCount cnt;
-  const bool ok = bin_mode == NLOS_BIN_SPLAT ? fwd_run<SCAN, COS, MODE_SPLAT>(a, b, e, sm, it, cnt)
-                                             : fwd_run<SCAN, COS, MODE_NEAREST>(a, b, e, sm, it, cnt);
+  const bool ok = fwd_run_ws<SCAN, COS, MODE>(a, b, e, sm, kServeStages, cnt, nullptr, it);
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
+  if ((threadIdx.x & 31) == 0 && cnt.tested) atomicAdd(a.pairs_tested, cnt.tested * 64ull);
   return ok;
+}
+
+template <int SCAN, int COS>
+__device__ bool fwd_item_cos(const FwdArgs& a, uint64_t b, uint64_t e, const FwdSmem& sm,
+                             uint32_t& it, int bin_mode) {
+  return bin_mode == NLOS_BIN_SPLAT ? fwd_item_mode<SCAN, COS, MODE_SPLAT>(a, b, e, sm, it)
+                                    : fwd_item_mode<SCAN, COS, MODE_NEAREST>(a, b, e, sm, it);
 }
 
 __device__ bool fwd_item(const JobDesc& j, uint64_t b, uint64_t e, const FwdSmem& sm,
                          uint32_t& it) {
   const FwdArgs& a = j.fwd;
+  const int m = j.bin_mode;
   if (j.scan_mode == NLOS_CONFOCAL) {
-    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_mode<NLOS_CONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, j.bin_mode);
-    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, j.bin_mode);
-    return fwd_item_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, j.bin_mode);
+    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, m);
+    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, m);
+    return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, m);
   }
-  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_mode<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, j.bin_mode);
-  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, j.bin_mode);
-  return fwd_item_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, j.bin_mode);
+  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, m);
+  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, m);
+  return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, m);
 }
 
 // REDUCE: transients [b, e) of the job, one warp per transient; the cube's
 // maximum and FP64 sums go to the job's scratch.
-__device__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t e) {
+__device__ __noinline__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t e) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t B = j.fwd.B;
   double csum = 0.0, csq = 0.0;
@@ -184,7 +212,7 @@ __device__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t e) {
 }
 
 // NOISE: bins [b, e) of the job; scale from the job's reduction.
-__device__ void noise_item(const JobDesc& j, uint64_t b, uint64_t e) {
+__device__ __noinline__ void noise_item(const JobDesc& j, uint64_t b, uint64_t e) {
   const float scale = noise_scale_from(j.scratch, j.noise_mode, j.peak_photons, j.nr_db, j.n);
   if (b == 0 && threadIdx.x == 0) {
     j.scratch->scale = scale;
@@ -196,44 +224,77 @@ __device__ void noise_item(const JobDesc& j, uint64_t b, uint64_t e) {
   }
 }
 
+// PACK: pairs [b, e) of the job (each item kind runs in its own frame, so
+// the FP64 paths' registers do not weigh on the forward's)
+__device__ __noinline__ void pack_item(const JobDesc& j, uint64_t b, uint64_t e) {
+  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x)
+    pack_pair(j.raw, j.P, k, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt,
+              const_cast<PointPair*>(j.fwd.pairs), &j.scratch->err);
+  // bounds of the sub-blocks this item packs (items start on sub-block edges)
+  const uint64_t sb_end = (e + kSubPairs - 1) / kSubPairs;
+  for (uint64_t sb = b / kSubPairs + (threadIdx.x >> 5); sb < sb_end; sb += blockDim.x >> 5)
+    block_bound_warp(j.raw, j.P, sb, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt, nullptr,
+                     const_cast<BlockBound*>(j.fwd.bounds) + sb);
+}
+
+// full[i] (one arrival: the producer's expect_tx) and empty[i] (one arrival
+// per consumer warp) for each stage.
+__device__ void init_stage_barriers(uint64_t* bars) {
+  for (int i = 0; i < kServeStages; ++i) {
+    mbar_init(&bars[i], 1);
+    mbar_init(&bars[kServeStages + i], kServeThreads / 32 - 1);
+  }
+  fence_mbar_init();
+}
+
 __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs q) {
   extern __shared__ __align__(128) unsigned char smem[];
   FwdSmem sm;
   sm.hist = reinterpret_cast<float*>(smem);
   sm.stage = reinterpret_cast<PointPair*>(smem + (size_t)kCapBw * kTile * 4);
-  sm.bars = reinterpret_cast<uint64_t*>(sm.stage + 2 * kPairsPerBlock);
-  JobDesc* jd = reinterpret_cast<JobDesc*>(sm.bars + 2);
+  sm.bars = reinterpret_cast<uint64_t*>(sm.stage + kServeStages * kServePpb);
+  sm.units = reinterpret_cast<unsigned long long*>(sm.bars + 2 * kServeStages);
+  JobDesc* jd = reinterpret_cast<JobDesc*>(sm.units + kServeStages + 1);
   __shared__ WorkItem s_item;
   __shared__ unsigned long long s_idx;
 
   const int tid = threadIdx.x;
   if (tid == 0) {
-    mbar_init(&sm.bars[0], 1);
-    mbar_init(&sm.bars[1], 1);
-    fence_mbar_init();
+    init_stage_barriers(sm.bars);
     atomicAdd_system(&q.ctl->alive, 1);
   }
   __syncthreads();
   uint32_t it = 0;
   uint32_t cached_job = 0xFFFFFFFFu, cached_gen = 0;
+  unsigned long long tail_seen = 0;  // thread 0: last tail read from host memory
+  unsigned long long cyc_wait = 0, cyc_fwd = 0, cyc_other = 0;  // thread 0
+  long long t_mark = clock64();
 
   for (;;) {
     if (tid == 0) {
+      // claim the next published index: compare-and-swap on the device head
+      // against a cached tail (it only grows, so a stale value is a safe
+      // bound); the tail in host memory is read again only when the head
+      // has caught up with the cached value
       unsigned long long got = kNone;
       const long long t0 = clock64();
+      unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(q.head);
       for (;;) {
-        const uint64_t tail = ld_acquire_sys(&q.ctl->tail);
-        const unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(q.head);
-        if (h < tail) {
-          if (atomicCAS(q.head, h, h + 1) == h) {
+        if (h < tail_seen) {
+          const unsigned long long seen = atomicCAS(q.head, h, h + 1);
+          if (seen == h) {
             got = h;
             break;
           }
+          h = seen;  // another CTA moved the head: retry from there
           continue;
         }
+        tail_seen = ld_acquire_sys(&q.ctl->tail);
+        if (h < tail_seen) continue;
         if (ld_volatile_u32(&q.ctl->park)) break;
         if (clock64() - t0 > kIdleCycles) break;
         __nanosleep(500);
+        h = *reinterpret_cast<volatile unsigned long long*>(q.head);
       }
       if (got != kNone) {
         // the slot is written before the tail moves; a withheld publication
@@ -253,6 +314,9 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         if (got != kSkip) s_item = *slot;
       }
       s_idx = got;
+      const long long now = clock64();
+      cyc_wait += (unsigned long long)(now - t_mark);
+      t_mark = now;
     }
     __syncthreads();
     const unsigned long long idx = s_idx;
@@ -279,16 +343,22 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
     }
     switch (item.kind) {
       case K_PACK:
-        for (uint64_t k = item.begin + tid; k < item.end; k += blockDim.x)
-          pack_pair(jd->raw, jd->P, k, jd->scan_mode, jd->cos_mode, jd->lx, jd->ly, jd->inv_cdt,
-                    const_cast<PointPair*>(jd->fwd.pairs), &jd->scratch->err);
+        pack_item(*jd, item.begin, item.end);
         break;
       case K_ZERO:
         for (uint64_t k = item.begin + tid; k < item.end; k += blockDim.x) jd->fwd.tau[k] = 0.0f;
         break;
       case K_FWD:
-        // a forward wait that gave up is recorded in the job error word
-        (void)fwd_item(*jd, item.begin, item.end, sm, it);
+        // a forward wait that gave up is recorded in the job error word; the
+        // stage barriers are then out of step with the unit counter: start
+        // them afresh (every copy has landed or been waited for, bounded)
+        if (!fwd_item(*jd, item.begin, item.end, sm, it)) {
+          if (tid == 0) {
+            for (int i = 0; i < 2 * kServeStages; ++i) mbar_inval(&sm.bars[i]);
+            init_stage_barriers(sm.bars);
+          }
+          it = 0;
+        }
         break;
       case K_REDUCE:
         reduce_item(*jd, item.begin, item.end);
@@ -302,9 +372,19 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       __threadfence_system();
       atomicAdd_system(&q.status[item.job].done[phase_of(item.kind)], 1u);
       atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed), 1ull);
+      const long long now = clock64();
+      if (item.kind == K_FWD) cyc_fwd += (unsigned long long)(now - t_mark);
+      else cyc_other += (unsigned long long)(now - t_mark);
+      t_mark = now;
     }
   }
-  if (tid == 0) atomicSub_system(&q.ctl->alive, 1);
+  if (tid == 0) {
+    cyc_wait += (unsigned long long)(clock64() - t_mark);
+    atomicAdd_system(&q.ctl->cycles[0], cyc_wait);
+    atomicAdd_system(&q.ctl->cycles[1], cyc_fwd);
+    atomicAdd_system(&q.ctl->cycles[2], cyc_other);
+    atomicSub_system(&q.ctl->alive, 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -331,8 +411,12 @@ struct Request {
   float* tau = nullptr;
   uint32_t* counts = nullptr;
   SceneScratch* scratch = nullptr;
+  BlockBound* bounds = nullptr;
+  TileBound* tiles = nullptr;
   SceneScratch* h_scratch = nullptr;  // pinned copy at completion (the slot's pool entry)
   cudaEvent_t ev = nullptr;
+  std::atomic<int> upload{0};  // 0 queued, 1 copies issued (ev recorded), 2 failed
+  std::string upload_msg;
   int phase = 0;
   uint32_t items[4] = {0, 0, 0, 0};
   uint32_t withheld = 0;  // published items that will never complete (fault injection)
@@ -356,6 +440,12 @@ struct Server {
   std::vector<int> free_slots;
   std::thread th;
   std::atomic<bool> stop{false};
+  // uploads run on their own thread: a copy from pageable memory returns only
+  // once the data is staged, and must not hold up the scheduler
+  std::vector<std::thread> uploaders;
+  std::mutex upmu;
+  std::condition_variable upcv;
+  std::deque<Request*> upq;
   uint64_t next_ticket = 1;
   int device = 0, num_sms = 0;
   cudaStream_t kstream = nullptr, cstream = nullptr;
@@ -398,6 +488,9 @@ void carve(Request* r) {
   size_t o_tau = take(sizeof(float) * g.S * g.B);
   size_t o_cnt = g.noise_mode != NLOS_NOISE_NONE ? take(sizeof(uint32_t) * g.S * g.B) : 0;
   size_t o_scr = take(sizeof(SceneScratch));
+  const uint64_t n_sub = (n_pairs + kSubPairs - 1) / kSubPairs;
+  size_t o_bnd = take(sizeof(BlockBound) * (n_sub ? n_sub : 1));
+  size_t o_til = take(sizeof(TileBound) * ((g.S + kTile - 1) / kTile));
   r->bytes = off;
   if (!r->dev) return;
   r->pairs = reinterpret_cast<PointPair*>(r->dev + o_pairs);
@@ -406,6 +499,8 @@ void carve(Request* r) {
   r->tau = reinterpret_cast<float*>(r->dev + o_tau);
   r->counts = g.noise_mode != NLOS_NOISE_NONE ? reinterpret_cast<uint32_t*>(r->dev + o_cnt) : nullptr;
   r->scratch = reinterpret_cast<SceneScratch*>(r->dev + o_scr);
+  r->bounds = reinterpret_cast<BlockBound*>(r->dev + o_bnd);
+  r->tiles = reinterpret_cast<TileBound*>(r->dev + o_til);
 }
 
 void fill_job(Server& sv, Request* r, JobDesc& j) {
@@ -419,12 +514,15 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   a.err = &r->scratch->err;
   a.boundary = &r->scratch->boundary_pairs;
   a.pairs_full = &r->scratch->pairs_full;
+  a.pairs_tested = &r->scratch->pairs_tested;
+  a.bounds = r->bounds;
+  a.tiles = r->tiles;
   a.n_pairs = (uint32_t)((g.P + 1) / 2);
   a.S = (uint32_t)g.S;
   a.B = g.B;
   a.kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
-  a.ppb = kPairsPerBlock;
-  a.stages = 2;
+  a.ppb = kServePpb;
+  a.stages = kServeStages;
   a.n_win = (g.B + kCapBw - 1) / kCapBw;
   a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
   a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
@@ -631,21 +729,13 @@ bool step(Server& sv) {
     r->h_scratch = sv.h_scratch + r->slot;
     std::memset(&sv.status[r->slot], 0, sizeof(JobStatus));
     // uploads on the copy stream (copy engines only: the serving kernel may be
-    // occupying every SM)
-    std::vector<ScanPoint> hs;
-    nlos::scan_points_host(r->params, r->g, hs);
-    SceneScratch zero{};
-    e = cudaMemcpyAsync(r->scan, hs.data(), sizeof(ScanPoint) * r->g.S, cudaMemcpyHostToDevice, sv.cstream);
-    if (e == cudaSuccess && r->g.P)
-      e = cudaMemcpyAsync(r->raw, r->pts.data(), sizeof(float) * 8 * r->g.P, cudaMemcpyHostToDevice, sv.cstream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(r->scratch, &zero, sizeof(zero), cudaMemcpyHostToDevice, sv.cstream);
-    if (e == cudaSuccess) e = cudaEventRecord(r->ev, sv.cstream);
-    if (e != cudaSuccess) {
-      free_request_memory(sv, r);
-      finish(sv, r, NLOS_ECUDA, cudaGetErrorString(e));
-      continue;
+    // occupying every SM), issued by the uploader thread
+    r->upload.store(0);
+    {
+      std::lock_guard<std::mutex> ul(sv.upmu);
+      sv.upq.push_back(r);
     }
+    sv.upcv.notify_one();
     r->state = R_UPLOAD;
     r->t_mark[0] = Clock::now();
     sv.active.push_back(r);
@@ -657,7 +747,12 @@ bool step(Server& sv) {
     Request* r = sv.active[i];
     bool leave = false;
     if (r->state == R_UPLOAD) {
-      if (cudaEventQuery(r->ev) == cudaSuccess) {
+      const int up = r->upload.load(std::memory_order_acquire);
+      if (up == 2) {
+        free_request_memory(sv, r);
+        finish(sv, r, NLOS_ECUDA, r->upload_msg);
+        leave = true;
+      } else if (up == 1 && cudaEventQuery(r->ev) == cudaSuccess) {
         r->pts.clear();
         r->pts.shrink_to_fit();
         fill_job(sv, r, sv.jobs[r->slot]);
@@ -725,6 +820,7 @@ bool step(Server& sv) {
         s.noise_dark = r->counts ? h.dark : 0.0;
         s.device_error = h.err;
         s.pairs_full = h.pairs_full;
+        s.pairs_tested = h.pairs_tested;
         if (h.err & kErrBadPoint) finish(sv, r, NLOS_EINVAL, "invalid surface point");
         else if (h.err & kErrWaitTimeout) finish(sv, r, NLOS_ETIMEOUT, "a bounded device wait gave up");
         else finish(sv, r, NLOS_OK, "");
@@ -755,6 +851,44 @@ bool step(Server& sv) {
   if (sv.active.empty() && sv.pending.empty())
     __atomic_store_n(&sv.ctl->park, 1u, __ATOMIC_RELEASE);
   return busy || !sv.active.empty();
+}
+
+// Uploader thread: scan table, points and a zeroed scratch of each admitted
+// request on the copy stream, then the request's event.
+void upload_loop(Server* sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> ul(sv->upmu);
+      sv->upcv.wait(ul, [&] { return sv->stop.load() || !sv->upq.empty(); });
+      if (sv->upq.empty()) return;  // stopping
+      r = sv->upq.front();
+      sv->upq.pop_front();
+    }
+    std::vector<ScanPoint> hs;
+    nlos::scan_points_host(r->params, r->g, hs);
+    std::vector<TileBound> ht;
+    nlos::tile_bounds_host(hs.data(), r->g.S, ht);
+    // the points in the spatial order the forward's unit culling relies on
+    std::vector<float> ordered(r->pts.size());
+    nlos::order_points_host(r->pts.data(), r->g.P, ordered.data());
+    SceneScratch zero{};
+    cudaError_t e = cudaMemcpyAsync(r->scan, hs.data(), sizeof(ScanPoint) * r->g.S,
+                                    cudaMemcpyHostToDevice, sv->cstream);
+    if (e == cudaSuccess && !ht.empty())
+      e = cudaMemcpyAsync(r->tiles, ht.data(), sizeof(TileBound) * ht.size(),
+                          cudaMemcpyHostToDevice, sv->cstream);
+    if (e == cudaSuccess && r->g.P)
+      e = cudaMemcpyAsync(r->raw, ordered.data(), sizeof(float) * 8 * r->g.P,
+                          cudaMemcpyHostToDevice, sv->cstream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->scratch, &zero, sizeof(zero), cudaMemcpyHostToDevice, sv->cstream);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev, sv->cstream);
+    if (e != cudaSuccess) r->upload_msg = cudaGetErrorString(e);
+    r->upload.store(e == cudaSuccess ? 1 : 2, std::memory_order_release);
+    sv->cv_work.notify_one();
+  }
 }
 
 void run(Server* sv) {
@@ -828,7 +962,8 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
   if ((e = cudaStreamCreateWithFlags(&sv.kstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
   if ((e = cudaStreamCreateWithFlags(&sv.cstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
   if ((e = cudaEventCreateWithFlags(&sv.kernel_done, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "cudaEventCreate");
-  sv.smem = (size_t)kCapBw * kTile * 4 + 2 * (size_t)kPairsPerBlock * sizeof(PointPair) + 16 + sizeof(JobDesc) + 64;
+  sv.smem = (size_t)kCapBw * kTile * 4 + kServeStages * (size_t)kServePpb * sizeof(PointPair) +
+            24 * kServeStages + 8 + sizeof(JobDesc) + 64;
   if ((e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sv.smem)) != cudaSuccess)
     return fail(e, "cudaFuncSetAttribute");
   cudaDeviceSynchronize();
@@ -836,6 +971,11 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
   sv.window = std::min<uint64_t>(kWindowPerSm * (uint64_t)sv.num_sms, kRing / 2);
   if (const char* tp = std::getenv("NLOS_SERVE_TRACE")) sv.trace = std::fopen(tp, "a");
   sv.th = std::thread(run, &sv);
+  // several uploaders: ordering a request's points on the host takes ~10 ns
+  // per point, and requests are independent
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  for (unsigned i = 0; i < std::min(4u, std::max(1u, hw / 4)); ++i)
+    sv.uploaders.emplace_back(upload_loop, &sv);
   *out = s;
   return NLOS_OK;
 }
@@ -946,6 +1086,12 @@ nlos_status nlos_server_destroy(nlos_server* server) {
   sv.stop.store(true);
   sv.cv_work.notify_all();
   if (sv.th.joinable()) sv.th.join();
+  {
+    std::lock_guard<std::mutex> ul(sv.upmu);
+    sv.upcv.notify_all();
+  }
+  for (std::thread& t : sv.uploaders)
+    if (t.joinable()) t.join();
   cudaStreamSynchronize(sv.kstream);  // the kernel exits once parked (bounded waits)
   cudaStreamSynchronize(sv.cstream);
   std::vector<Request*> all;
@@ -983,6 +1129,14 @@ nlos_status nlos_server_stats(nlos_server* server, uint64_t* resident_bytes, uin
   if (resident_bytes) *resident_bytes = server->sv.resident;
   if (pending) *pending = (uint32_t)server->sv.pending.size();
   if (active) *active = (uint32_t)server->sv.active.size();
+  return NLOS_OK;
+}
+
+nlos_status nlos_server_device_cycles(nlos_server* server, uint64_t cycles_out[3]) {
+  clear_error();
+  if (!server || !cycles_out) return set_error(NLOS_EINVAL, "server or cycles_out is NULL");
+  const Control* c = server->sv.ctl;
+  for (int k = 0; k < 3; ++k) cycles_out[k] = __atomic_load_n(&c->cycles[k], __ATOMIC_ACQUIRE);
   return NLOS_OK;
 }
 

@@ -69,6 +69,7 @@ class Stats(ctypes.Structure):
         ("variance", ctypes.c_double), ("boundary_pairs", ctypes.c_uint64),
         ("device_error", ctypes.c_uint32),
         ("pairs_full", ctypes.c_uint64),
+        ("pairs_tested", ctypes.c_uint64),
     ]
 
     def to_dict(self) -> dict:
@@ -126,6 +127,7 @@ def load(path: str | None = None):
             "nlos_server_stats": (S, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U32),
                                       ctypes.POINTER(_U32)]),
             "nlos_server_inject": (S, [_P, ctypes.c_int]),
+            "nlos_server_device_cycles": (S, [_P, ctypes.POINTER(_U64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -361,6 +363,11 @@ class Server:
         _check(_lib.nlos_server_stats(self.handle, ctypes.byref(r), ctypes.byref(p),
                                       ctypes.byref(a)))
         return dict(resident_bytes=r.value, pending=p.value, active=a.value)
+
+    def device_cycles(self) -> dict:
+        c = (_U64 * 3)()
+        _check(_lib.nlos_server_device_cycles(self.handle, c))
+        return dict(wait=c[0], forward=c[1], other=c[2])
 
     def inject(self, fault: int):
         _check(_lib.nlos_server_inject(self.handle, int(fault)))

@@ -221,17 +221,19 @@ def test_paper_dataset_shape():
 
 
 def test_early_out_count():
-    """The forward skips (warp, point pair) groups that no lane can bin and
-    reports the pairs it evaluated in full: a multiple of 64, within the padded
-    pair count, and zero when the window lies beyond every path."""
+    """The forward rules out (tile, block) units from their bounds and skips
+    (warp, point pair) groups that no lane can bin; it reports the pairs of the
+    units it staged and the pairs it evaluated in full: multiples of 64, within
+    the padded pair count, and zero when the window lies beyond every path."""
     params, pts = scenes.workload_union64()
     g = H.gpu_forward(params, pts, stats=True)
-    full = g["stats"]["pairs_full"]
+    full, tested = g["stats"]["pairs_full"], g["stats"]["pairs_tested"]
     S, P = g["tau"].shape[0], pts.shape[0]
-    assert full % 64 == 0
-    assert 0 < full <= ((S + 31) // 32 * 32) * ((P + 1) // 2 * 2)
-    print("union64 pairs evaluated in full:", full / (S * P))
+    assert full % 64 == 0 and tested % 64 == 0
+    assert 0 < full <= tested <= ((S + 31) // 32 * 32) * ((P + 1) // 2 * 2)
+    print("union64 pairs evaluated in full:", full / (S * P), "in staged units:", tested / (S * P))
     far = dict(params, window_start_m=100.0)
     g2 = H.gpu_forward(far, pts, stats=True)
-    assert g2["stats"]["pairs_full"] == 0
+    # every unit is ruled out from the bounds: no pair is touched
+    assert g2["stats"]["pairs_full"] == 0 and g2["stats"]["pairs_tested"] == 0
     assert not g2["tau"].any()
