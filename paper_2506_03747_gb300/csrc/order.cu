@@ -25,7 +25,6 @@ namespace nlos {
 
 namespace {
 
-constexpr uint32_t kBoxWords = 8;  // after the cell counts: min x,y,z, max x,y,z (ordered bits)
 
 // float -> unsigned with the same order
 __host__ __device__ inline uint32_t ord_bits(float f) {
@@ -64,7 +63,8 @@ __host__ __device__ inline void box_scale(const float* lo, const float* hi, floa
   }
 }
 
-__global__ void box_kernel(const float* __restrict__ raw, uint64_t P, uint32_t* box) {
+__global__ void __launch_bounds__(256) box_kernel(const float* __restrict__ raw, uint64_t P,
+                                                  uint32_t* box) {
   uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -79,11 +79,23 @@ __global__ void box_kernel(const float* __restrict__ raw, uint64_t P, uint32_t* 
       mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
       mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
     }
+  // CTA reduction first: one global atomic per CTA and word (same-address
+  // atomics from every warp serialise)
+  __shared__ uint32_t s[8][6];
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
     for (int c = 0; c < 3; ++c) {
-      atomicMin(&box[c], mn[c]);
-      atomicMax(&box[3 + c], mx[c]);
+      s[w][c] = mn[c];
+      s[w][3 + c] = mx[c];
     }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int c = threadIdx.x;
+    uint32_t v = s[0][c];
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) v = c < 3 ? min(v, s[j][c]) : max(v, s[j][c]);
+    if (c < 3) atomicMin(&box[c], v);
+    else atomicMax(&box[c], v);
+  }
 }
 
 __global__ void cell_kernel(const float* __restrict__ raw, uint64_t P, const uint32_t* box,
@@ -102,29 +114,39 @@ __global__ void cell_kernel(const float* __restrict__ raw, uint64_t P, const uin
   }
 }
 
-// One CTA of 1024 threads: counts[c] <- sum of counts[0..c) (32 cells each).
+// One CTA of 1024 threads: counts[c] <- sum of counts[0..c). Warp w scans
+// cells [w * 1024, (w + 1) * 1024) 32 at a time (coalesced loads, shuffle
+// scans), then the 32 warp totals are scanned.
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* counts) {
-  constexpr int kPer = kOrderCells / 1024;
-  __shared__ uint32_t part[1024];
-  uint32_t v[kPer], s = 0;
-  for (int j = 0; j < kPer; ++j) {
-    v[j] = counts[threadIdx.x * kPer + j];
-    s += v[j];
+  constexpr int kPerWarp = kOrderCells / 32;
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* seg = counts + (size_t)w * kPerWarp;
+  uint32_t carry = 0;
+  for (int j = 0; j < kPerWarp; j += 32) {
+    const uint32_t v = seg[j + lane];
+    uint32_t x = v;  // inclusive scan of the 32 values
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    seg[j + lane] = carry + x - v;  // exclusive within the warp's segment
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  part[threadIdx.x] = s;
+  if (lane == 0) wsum[w] = carry;
   __syncthreads();
-  // inclusive Hillis-Steele scan of the 1024 partial sums
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += add;
-    __syncthreads();
+  if (w == 0) {
+    const uint32_t v = wsum[lane];
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x - v;
   }
-  uint32_t base = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-  for (int j = 0; j < kPer; ++j) {
-    counts[threadIdx.x * kPer + j] = base;
-    base += v[j];
-  }
+  __syncthreads();
+  const uint32_t base = wsum[w];
+  for (int j = lane; j < kPerWarp; j += 32) seg[j] += base;
 }
 
 __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* cursor, uint32_t* perm) {
@@ -171,7 +193,7 @@ cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(box, 0xff, sizeof(uint32_t) * 3, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(box + 3, 0, sizeof(uint32_t) * 3, st);
   if (e != cudaSuccess) return e;
-  box_kernel<<<grid_for(P, 256, s.num_sms), 256, 0, st>>>(s.raw_points, P, box);
+  box_kernel<<<grid_for(P, 2048, s.num_sms), 256, 0, st>>>(s.raw_points, P, box);
   cell_kernel<<<grid_for(P, 256, s.num_sms), 256, 0, st>>>(s.raw_points, P, box, s.cell, counts);
   scan_kernel<<<1, 1024, 0, st>>>(counts);
   scatter_kernel<<<grid_for(P, 256, s.num_sms), 256, 0, st>>>(s.cell, P, counts, s.perm);
