@@ -51,7 +51,7 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #define NLOS_FWD_VOTE 0                     // 2: warp-uniform skip before the reductions
 #endif
 #ifndef NLOS_FWD_CHUNKS_PER_CTA
-#define NLOS_FWD_CHUNKS_PER_CTA 16          // standalone forward: claimed chunks per CTA (mean)
+#define NLOS_FWD_CHUNKS_PER_CTA 32          // standalone forward: claimed chunks per CTA (mean)
 #endif
 #ifndef NLOS_FWD_STAGES
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
@@ -353,10 +353,68 @@ __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int la
   }
 }
 
+// Four output bins o0..o0+3 of one column: each histogram row read once
+// (4 + 2R loads into registers), the taps unrolled at compile time.
+template <int R>
+__device__ __forceinline__ void conv_quad(const FwdArgs& a, const float* hist, int r0, int bw, int c,
+                                          float v[4]) {
+  float h[4 + 2 * R];
+#pragma unroll
+  for (int k = 0; k < 4 + 2 * R; ++k) {
+    const int b = r0 - R + k;
+    h[k] = (b >= 0 && b < bw) ? hist[b * kTile + c] : 0.f;
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = -R; j <= R; ++j) acc = fmaf(a.taps[j + R], h[e - j + R], acc);
+    v[e] = acc;
+  }
+}
+
+// Any radius (taps loop at run time).
+__device__ __forceinline__ void conv_quad_any(const FwdArgs& a, const float* hist, int r0, int bw,
+                                              int c, int R, float v[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int bc = r0 + e;  // histogram row of the centre tap
+    float acc = 0.f;
+    for (int j = -R; j <= R; ++j) {
+      const int b = bc - j;
+      if (b >= 0 && b < bw) acc = fmaf(a.taps[j + R], hist[b * kTile + c], acc);
+    }
+    v[e] = acc;
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void flush_quads(const FwdArgs& a, const float* hist, int lo, int nq,
+                                            int w0, int R_rt, uint32_t s, int c, int warp_rel,
+                                            int n_warps) {
+  for (int qi = warp_rel; qi < nq; qi += n_warps) {
+    const int o0 = lo + 4 * qi;
+    float v[4];
+    if (R >= 0) conv_quad<(R >= 0 ? R : 0)>(a, hist, o0 - w0, (int)a.bw, c, v);
+    else conv_quad_any(a, hist, o0 - w0, (int)a.bw, c, R_rt, v);
+    if (s < a.S && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)) {
+      float* dst = a.tau + (size_t)s * a.B + o0;
+      if ((a.B & 3u) == 0u) {
+        red_add_global_v4(dst, make_float4(v[0], v[1], v[2], v[3]));
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (o0 + e < (int)a.B && o0 + e >= 0) red_add_global(dst + e, v[e]);
+      }
+    }
+  }
+}
+
 // Flush the partial histogram of (tile, window) tw into tau (jittered for
 // NEAREST): out[o] = sum_j taps[j + R] * hist[o - w0 - j], zero outside the
 // window; four consecutive bins per thread, one vector reduction each. Runs
-// on the warps [w_first, w_first + n_warps) of the CTA.
+// on the warps [w_first, w_first + n_warps) of the CTA. Radii up to 16 use
+// a compile-time unrolled convolution.
 template <int MODE>
 __device__ __forceinline__ void flush_tile(const FwdArgs& a, long long tw, const float* hist,
                                            int warp_rel, int n_warps) {
@@ -369,30 +427,19 @@ __device__ __forceinline__ void flush_tile(const FwdArgs& a, long long tw, const
   const int nq = (hi - lo + 3) >> 2;  // quads of output bins
   const int c = threadIdx.x & 31;
   const uint32_t s = tile * kTile + c;
-  for (int qi = warp_rel; qi < nq; qi += n_warps) {
-    const int o0 = lo + 4 * qi;
-    float v[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int bc = o0 + e - w0;  // histogram row of the centre tap
-      float acc = 0.f;
-      for (int j = -R; j <= R; ++j) {
-        const int b = bc - j;
-        if (b >= 0 && b < (int)a.bw) acc = fmaf(a.taps[j + R], hist[b * kTile + c], acc);
-      }
-      v[e] = acc;
-    }
-    if (s < a.S && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)) {
-      float* dst = a.tau + (size_t)s * a.B + o0;
-      if ((a.B & 3u) == 0u) {
-        red_add_global_v4(dst, make_float4(v[0], v[1], v[2], v[3]));
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (o0 + e < (int)a.B && o0 + e >= 0) red_add_global(dst + e, v[e]);
-      }
-    }
+#define NLOS_FLUSH_R(RR) \
+  case RR:               \
+    flush_quads<RR>(a, hist, lo, nq, w0, R, s, c, warp_rel, n_warps); \
+    break;
+  switch (R) {
+    NLOS_FLUSH_R(0) NLOS_FLUSH_R(1) NLOS_FLUSH_R(2) NLOS_FLUSH_R(3) NLOS_FLUSH_R(4)
+    NLOS_FLUSH_R(5) NLOS_FLUSH_R(6) NLOS_FLUSH_R(7) NLOS_FLUSH_R(8) NLOS_FLUSH_R(9)
+    NLOS_FLUSH_R(10) NLOS_FLUSH_R(11) NLOS_FLUSH_R(12) NLOS_FLUSH_R(13) NLOS_FLUSH_R(14)
+    NLOS_FLUSH_R(15) NLOS_FLUSH_R(16)
+    default:
+      flush_quads<-1>(a, hist, lo, nq, w0, R, s, c, warp_rel, n_warps);
   }
+#undef NLOS_FLUSH_R
 }
 
 // All pairs of one staged block for this warp (pairs warp_rel, warp_rel +
