@@ -96,6 +96,8 @@ def _load():
                                                ctypes.c_int]
             lib.orc_jitter_taps.argtypes = [_D, _D, _P, ctypes.c_int]
             lib.orc_jitter.argtypes = [_P, _I64, ctypes.c_int32, _P, ctypes.c_int32, _P]
+            lib.orc_jitter_padded.argtypes = [_P, _I64, ctypes.c_int32, _P, ctypes.c_int32,
+                                              ctypes.c_int32, _P]
             lib.orc_philox4x32_10.argtypes = [_P, _P, _P]
             lib.orc_noise_lambda.argtypes = [_P, _I64, ctypes.c_float, ctypes.c_float, _P]
             lib.orc_poisson_one.argtypes = [ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64,
@@ -201,14 +203,19 @@ def jitter_taps(fwhm_s: float, bin_width_s: float) -> np.ndarray:
     return buf[:k].copy()
 
 
-def jitter(tau: np.ndarray, taps: np.ndarray) -> np.ndarray:
+PADDINGS = {"zero": 0, "replicate": 1}
+
+
+def jitter(tau: np.ndarray, taps: np.ndarray, padding: str = "zero") -> np.ndarray:
+    """Gaussian jitter along the last axis (Eq. 16/17) with zero padding (the
+    default reading) or the edge bins replicated outside the window."""
     lib = _load()
     t = np.ascontiguousarray(tau, dtype=np.float64)
     B = t.shape[-1]
     n = t.size // B
     out = np.zeros_like(t)
     tp = np.ascontiguousarray(taps, dtype=np.float64)
-    lib.orc_jitter(_ptr(t), n, B, _ptr(tp), tp.size, _ptr(out))
+    lib.orc_jitter_padded(_ptr(t), n, B, _ptr(tp), tp.size, PADDINGS[padding], _ptr(out))
     return out
 
 
@@ -311,7 +318,7 @@ def simulate(params, pts, s_begin: int = 0, s_count: int | None = None, threads:
     r = forward_binned(params, pts, s_begin, s_count, threads=threads)
     tau = r["tau"]
     taps = jitter_taps(params["jitter_fwhm_s"], params["bin_width_s"])
-    tau_g = jitter(tau, taps)
+    tau_g = jitter(tau, taps, params.get("jitter_padding", "zero"))
     out = dict(tau=tau, tau_g=tau_g, energy=tau_g.sum(axis=1), taps=taps)
     if with_noise and params["noise_mode"] != "none":
         lam, scale, dark = noise_lambda(tau_g, params)

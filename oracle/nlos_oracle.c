@@ -183,8 +183,8 @@ int orc_jitter_taps(double fwhm_s, double bin_width_s, double* taps, int max_tap
 }
 
 /* out[s][b] = sum_j taps[j + R] * tau[s][b - j], j = -R..R, zero outside [0, B). */
-void orc_jitter(const double* tau, int64_t num_traces, int32_t num_bins,
-                const double* taps, int32_t k, double* out) {
+void orc_jitter_padded(const double* tau, int64_t num_traces, int32_t num_bins,
+                       const double* taps, int32_t k, int32_t padding, double* out) {
   int32_t R = (k - 1) / 2;
   for (int64_t s = 0; s < num_traces; ++s) {
     const double* in = tau + s * num_bins;
@@ -193,11 +193,20 @@ void orc_jitter(const double* tau, int64_t num_traces, int32_t num_bins,
       double acc = 0.0;
       for (int32_t j = -R; j <= R; ++j) {
         int32_t src = b - j;
+        if (padding == 1) {  /* replicate: the edge bins continue outside */
+          if (src < 0) src = 0;
+          if (src > num_bins - 1) src = num_bins - 1;
+        }
         if (src >= 0 && src < num_bins) acc += taps[j + R] * in[src];
       }
       o[b] = acc;
     }
   }
+}
+
+void orc_jitter(const double* tau, int64_t num_traces, int32_t num_bins,
+                const double* taps, int32_t k, double* out) {
+  orc_jitter_padded(tau, num_traces, num_bins, taps, k, 0, out);
 }
 
 /* ---------------------------------------------------------------------------

@@ -64,6 +64,10 @@ int orc_forward_binned(const orc_geom* g, int64_t num_points, const double* pts,
 int orc_jitter_taps(double fwhm_s, double bin_width_s, double* taps, int max_taps);
 void orc_jitter(const double* tau, int64_t num_traces, int32_t num_bins,
                 const double* taps, int32_t k, double* out);
+/* The same with a boundary rule: padding 0 = zero padding (Eq. 17 fixes only
+ * k; zero padding is the default reading), 1 = replicate the edge bins. */
+void orc_jitter_padded(const double* tau, int64_t num_traces, int32_t num_bins,
+                       const double* taps, int32_t k, int32_t padding, double* out);
 
 /* Philox4x32-10 (Salmon et al., SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

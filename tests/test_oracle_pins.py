@@ -224,6 +224,34 @@ def test_jitter_taps_and_scipy():
     np.testing.assert_allclose(oracle.jitter(x, taps), ref, rtol=1e-12, atol=1e-15)
 
 
+def test_jitter_replicate_padding():
+    """Replicate padding (the edge bins continue outside the window): a constant
+    transient is unchanged, an edge impulse keeps the taps that fall outside,
+    and scipy's 'nearest' mode with the same radius agrees."""
+    scipy_nd = pytest.importorskip("scipy.ndimage")
+    fwhm, dt = 70e-12, 8e-12
+    taps = oracle.jitter_taps(fwhm, dt)
+    R = (taps.size - 1) // 2
+    const = np.full((2, 40), 3.25)
+    np.testing.assert_allclose(oracle.jitter(const, taps, "replicate"), const, rtol=1e-15)
+    imp = np.zeros((1, 40))
+    imp[0, 0] = 1.0
+    out = oracle.jitter(imp, taps, "replicate")[0]
+    # bin b receives taps j >= b (sources b - j <= 0 all read bin 0)
+    np.testing.assert_allclose(out[:R + 1], [taps[R + b:].sum() for b in range(R + 1)],
+                               rtol=1e-14)
+    # total: tap j (0 <= j <= R) reaches bins 0..j
+    assert out.sum() == pytest.approx(taps[R:] @ (np.arange(R + 1) + 1.0), rel=1e-14)
+    rng = np.random.default_rng(4)
+    x = rng.random((5, 150))
+    sg = oracle.sigma_bins(fwhm, dt)
+    ref = scipy_nd.gaussian_filter1d(x, sg, axis=1, mode="nearest", truncate=R / sg)
+    np.testing.assert_allclose(oracle.jitter(x, taps, "replicate"), ref, rtol=1e-12, atol=1e-15)
+    # zero padding differs only within R of the edges
+    z = oracle.jitter(x, taps)
+    np.testing.assert_array_equal(z[:, R:-R], oracle.jitter(x, taps, "replicate")[:, R:-R])
+
+
 def test_jitter_energy_leak_at_window_edges():
     taps = oracle.jitter_taps(60e-12, 8e-12)
     R = (taps.size - 1) // 2
