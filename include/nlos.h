@@ -111,6 +111,10 @@ typedef struct {
   uint32_t stream_tag;        /* word 3 of every Philox counter */
   float boundary_eps;         /* > 0: count pairs with u within eps of a bin
                                  edge (nlos_stats.boundary_pairs); 0 = off */
+  int32_t jitter_padding;     /* boundary rule of the jitter (Eq. 17 gives only
+                                 the kernel length): 0 = zero padding (default),
+                                 1 = the edge bins continue outside the window
+                                 (replicate); NEAREST binning only */
 } nlos_params;
 
 /* Fills *p with the defaults: 32x32 confocal scan of a 1 m x 1 m wall, no
@@ -212,6 +216,12 @@ nlos_status nlos_simulate_backward(nlos_scene* scene, const float* grad_tau_dev,
  * in and out are [num_traces][num_bins] float32 device and must not overlap. */
 nlos_status nlos_jitter(const float* in_dev, float* out_dev, uint64_t num_traces,
                         uint32_t num_bins, double fwhm_s, double bin_width_s, void* cuda_stream);
+
+/* nlos_jitter with a boundary rule: padding 0 = zero padding (as nlos_jitter),
+ * 1 = replicate (in[b] for b < 0 reads in[0], for b >= num_bins in[num_bins-1]). */
+nlos_status nlos_jitter_padded(const float* in_dev, float* out_dev, uint64_t num_traces,
+                               uint32_t num_bins, double fwhm_s, double bin_width_s,
+                               int32_t padding, void* cuda_stream);
 
 /* Per-trace FP64 energy (energy_dev [num_traces], nullable) and the cube's
  * maximum and FP64 sum / sum of squares (written to stats_dev, nullable:

@@ -222,17 +222,32 @@ nlos_status nlos_simulate_backward(nlos_scene* scene, const float* grad_tau_dev,
   return NLOS_OK;
 }
 
-nlos_status nlos_jitter(const float* in_dev, float* out_dev, uint64_t num_traces,
-                        uint32_t num_bins, double fwhm_s, double bin_width_s, void* cuda_stream) {
+static nlos_status jitter_entry(const float* in_dev, float* out_dev, uint64_t num_traces,
+                                uint32_t num_bins, double fwhm_s, double bin_width_s, int padding,
+                                void* cuda_stream) {
   clear_error();
   if (!in_dev || !out_dev) return set_error(NLOS_EINVAL, "in_dev and out_dev must not be NULL");
   if (in_dev == out_dev) return set_error(NLOS_EINVAL, "in_dev and out_dev must not overlap");
   if (!(std::isfinite(fwhm_s) && fwhm_s >= 0 && std::isfinite(bin_width_s) && bin_width_s > 0))
     return set_error(NLOS_EINVAL, "fwhm_s must be >= 0 and bin_width_s > 0");
+  if (padding != 0 && padding != 1) return set_error(NLOS_EINVAL, "padding must be 0 or 1");
   const double sigma = fwhm_s > 0 ? fwhm_s / (2.0 * std::sqrt(2.0 * std::log(2.0)) * bin_width_s) : 0.0;
   if (jitter_radius(sigma) > 1024) return set_error(NLOS_EINVAL, "jitter kernel radius above 1024 bins");
-  NLOS_CUDA_TRY(launch_jitter(in_dev, out_dev, num_traces, num_bins, sigma, as_stream(cuda_stream)));
+  NLOS_CUDA_TRY(launch_jitter(in_dev, out_dev, num_traces, num_bins, sigma, padding,
+                              as_stream(cuda_stream)));
   return NLOS_OK;
+}
+
+nlos_status nlos_jitter(const float* in_dev, float* out_dev, uint64_t num_traces,
+                        uint32_t num_bins, double fwhm_s, double bin_width_s, void* cuda_stream) {
+  return jitter_entry(in_dev, out_dev, num_traces, num_bins, fwhm_s, bin_width_s, 0, cuda_stream);
+}
+
+nlos_status nlos_jitter_padded(const float* in_dev, float* out_dev, uint64_t num_traces,
+                               uint32_t num_bins, double fwhm_s, double bin_width_s,
+                               int32_t padding, void* cuda_stream) {
+  return jitter_entry(in_dev, out_dev, num_traces, num_bins, fwhm_s, bin_width_s, padding,
+                      cuda_stream);
 }
 
 nlos_status nlos_reduce(const float* tau_dev, uint64_t num_traces, uint32_t num_bins,

@@ -126,7 +126,11 @@ cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* g
 // Detector kernels (detector.cu).
 int jitter_taps(double sigma, float* taps, int max_taps);  // returns k
 cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t B, double sigma,
-                          cudaStream_t st);
+                          int replicate, cudaStream_t st);
+// Replicate-padding correction weights of a jitter kernel: tail[k] = sum of the
+// taps at offsets k + 1 .. R (k < R), i.e. the weight that output bin k (or
+// B - 1 - k) draws from beyond the first (or last) bin.
+void jitter_tails(const float* taps, int R, float* tail);
 cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double* energy,
                           SceneScratch* scratch, cudaStream_t st);
 cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,

@@ -37,6 +37,14 @@ int jitter_taps(double sigma, float* taps, int max_taps) {
   return k;
 }
 
+void jitter_tails(const float* taps, int R, float* tail) {
+  double acc = 0.0;  // running sum from the outermost tap inwards
+  for (int k = R - 1; k >= 0; --k) {
+    acc += (double)taps[R + k + 1];
+    tail[k] = (float)acc;
+  }
+}
+
 constexpr int kJitterMaxTaps = 2049;  // R <= 1024 bins
 constexpr int kJitterTile = 1024;
 
@@ -46,6 +54,7 @@ struct JitterArgs {
   uint64_t traces;
   uint32_t B;
   int R;
+  int replicate;  // 1: the edge bins continue outside the trace
   float taps[kJitterMaxTaps];
 };
 
@@ -59,7 +68,8 @@ __global__ void jitter_kernel(const __grid_constant__ JitterArgs a) {
   const float* row = a.in + t * a.B;
   for (int i = threadIdx.x; i < kJitterTile + 2 * a.R; i += blockDim.x) {
     const int b = b0 - a.R + i;
-    sm[i] = (b >= 0 && b < (int)a.B) ? row[b] : 0.0f;
+    if (a.replicate) sm[i] = row[min(max(b, 0), (int)a.B - 1)];
+    else sm[i] = (b >= 0 && b < (int)a.B) ? row[b] : 0.0f;
   }
   __syncthreads();
   float* orow = a.out + t * a.B;
@@ -74,13 +84,14 @@ __global__ void jitter_kernel(const __grid_constant__ JitterArgs a) {
 }
 
 cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t B, double sigma,
-                          cudaStream_t st) {
+                          int replicate, cudaStream_t st) {
   if (traces == 0 || B == 0) return cudaSuccess;
   JitterArgs a;
   a.in = in;
   a.out = out;
   a.traces = traces;
   a.B = B;
+  a.replicate = replicate;
   const int k = jitter_taps(sigma, a.taps, kJitterMaxTaps);
   if (k < 0) return cudaErrorInvalidValue;
   a.R = (k - 1) / 2;

@@ -189,6 +189,8 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   } else {
     a.R = jitter_taps(g.sigma, a.taps, kMaxTaps);
     a.R = (a.R - 1) / 2;
+    a.replicate = sc.params.jitter_padding == 1;
+    if (a.replicate) jitter_tails(a.taps, a.R, a.tail);
   }
 
   // shared memory: histogram [bw][32] floats + two staged blocks + barriers

@@ -115,6 +115,8 @@ struct FwdArgs {
   float reach;       // splat: 6 sigma
   float qstep;       // splat: exp(-1 / sigma^2)
   float taps[kMaxTaps];
+  int replicate;     // jitter with the edge bins continued outside the window
+  float tail[kMaxTaps / 2 + 1];  // replicate corrections (jitter_tails)
 };
 
 struct bool2_t {
@@ -397,6 +399,18 @@ __device__ __forceinline__ void flush_quads(const FwdArgs& a, const float* hist,
     float v[4];
     if (R >= 0) conv_quad<(R >= 0 ? R : 0)>(a, hist, o0 - w0, (int)a.bw, c, v);
     else conv_quad_any(a, hist, o0 - w0, (int)a.bw, c, R_rt, v);
+    if (a.replicate) {
+      // the taps beyond the first / last bin read that bin (linear, so each
+      // partial histogram adds its own share); only the windows holding it
+      const int last = (int)a.B - 1;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int o = o0 + e;
+        if (w0 == 0 && o < R_rt) v[e] = fmaf(a.tail[o], hist[c], v[e]);
+        if (last - w0 < (int)a.bw && last - o >= 0 && last - o < R_rt)
+          v[e] = fmaf(a.tail[last - o], hist[(last - w0) * kTile + c], v[e]);
+      }
+    }
     if (s < a.S && (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)) {
       float* dst = a.tau + (size_t)s * a.B + o0;
       if ((a.B & 3u) == 0u) {

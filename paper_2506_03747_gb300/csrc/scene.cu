@@ -50,6 +50,8 @@ nlos_status resolve(const nlos_params& p, uint64_t num_points, Geometry& g) {
     return set_error(NLOS_EINVAL, "peak_photons, dark_per_bin must be finite and >= 0; nr_db finite");
   if (!(std::isfinite(p.boundary_eps) && p.boundary_eps >= 0 && p.boundary_eps < 0.5f))
     return set_error(NLOS_EINVAL, "boundary_eps must be in [0, 0.5)");
+  if (p.jitter_padding != 0 && p.jitter_padding != 1)
+    return set_error(NLOS_EINVAL, "jitter_padding must be 0 (zero) or 1 (replicate)");
   if (num_points > (uint64_t)1 << 31)
     return set_error(NLOS_EINVAL, "num_points must be <= 2^31");
 

@@ -527,6 +527,7 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
   a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
   a.units = (unsigned long long)((g.S + kTile - 1) / kTile) * a.n_win * a.n_blk;
+  a.replicate = 0;
   if (g.bin_mode == NLOS_BIN_SPLAT) {
     const double s = g.sigma;
     a.inv2s2 = (float)(1.0 / (2.0 * s * s));
@@ -537,6 +538,8 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
     a.taps[0] = 1.0f;
   } else {
     a.R = (jitter_taps(g.sigma, a.taps, kMaxTaps) - 1) / 2;
+    a.replicate = r->params.jitter_padding == 1;
+    if (a.replicate) jitter_tails(a.taps, a.R, a.tail);
   }
   j.raw = r->raw;
   j.counts = r->counts;

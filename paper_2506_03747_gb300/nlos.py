@@ -57,6 +57,7 @@ class Params(ctypes.Structure):
         ("nr_db", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("stream_tag", ctypes.c_uint32),
         ("boundary_eps", ctypes.c_float),
+        ("jitter_padding", ctypes.c_int32),
     ]
 
 
@@ -111,6 +112,8 @@ def load(path: str | None = None):
             "nlos_detect": (S, [_P, _P, _P, _P, _P]),
             "nlos_simulate_backward": (S, [_P, _P, _P, _P, _P]),
             "nlos_jitter": (S, [_P, _P, _U64, _U32, ctypes.c_double, ctypes.c_double, _P]),
+            "nlos_jitter_padded": (S, [_P, _P, _U64, _U32, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int32, _P]),
             "nlos_reduce": (S, [_P, _U64, _U32, _P, _P, _P]),
             "nlos_reduce_static": (S, [_P, _U64, _U32, _P, _P, _P]),
             "nlos_noise": (S, [_P, _U64, ctypes.c_float, ctypes.c_float, _U64, _U32, _U64, _P,
@@ -172,6 +175,7 @@ _ENUM = {
     "bin_mode": {"nearest": BIN_NEAREST, "splat": BIN_SPLAT},
     "cos_mode": {"none": COS_NONE, "object": COS_OBJECT, "object_wall": COS_OBJECT_WALL},
     "noise_mode": {"none": NOISE_NONE, "peak": NOISE_PEAK, "paper_nr": NOISE_PAPER_NR},
+    "jitter_padding": {"zero": 0, "replicate": 1},
 }
 
 
@@ -291,9 +295,14 @@ def simulate_backward(scene: Scene, grad_tau, grad_albedo=None, grad_depth=None,
 
 
 def jitter(inp, out, num_traces: int, num_bins: int, fwhm_s: float, bin_width_s: float,
-           stream=None):
-    _check(load().nlos_jitter(_ptr(inp), _ptr(out), num_traces, num_bins, float(fwhm_s),
-                              float(bin_width_s), _stream(stream)))
+           stream=None, padding: str = "zero"):
+    if padding == "zero":
+        _check(load().nlos_jitter(_ptr(inp), _ptr(out), num_traces, num_bins, float(fwhm_s),
+                                  float(bin_width_s), _stream(stream)))
+    else:
+        _check(load().nlos_jitter_padded(_ptr(inp), _ptr(out), num_traces, num_bins,
+                                         float(fwhm_s), float(bin_width_s),
+                                         _ENUM["jitter_padding"][padding], _stream(stream)))
 
 
 def reduce(tau, num_traces: int, num_bins: int, energy=None, stats=None, stream=None):

@@ -39,6 +39,7 @@ def default_params(**kw) -> dict:
         num_bins=256,
         window_start_m=float("nan"),   # NaN: device legs of the wall centre
         jitter_fwhm_s=0.0,
+        jitter_padding="zero",         # or "replicate" (the edge bins continue outside)
         bin_mode="nearest",            # or "splat"
         cos_mode="object",             # "none", "object", "object_wall"
         noise_mode="none",             # "none", "peak", "paper_nr"

@@ -116,6 +116,7 @@ def oracle_with_allowance(params, pts, s_begin=0, s_count=None, threads=0):
     r = oracle.forward_binned(params, pts, s_begin, s_count, eps=u_eps(int(params["num_bins"])),
                               threads=threads)
     taps = oracle.jitter_taps(params["jitter_fwhm_s"], params["bin_width_s"])
-    return dict(tau=r["tau"], flip=r["flip_mass"], edge=r["edge_mass"], taps=taps,
-                tau_g=oracle.jitter(r["tau"], taps), flip_g=oracle.jitter(r["flip_mass"], taps),
-                n_boundary=r["n_boundary"])
+    pad = params.get("jitter_padding", "zero")
+    return dict(tau=r["tau"], flip=r["flip_mass"], edge=r["edge_mass"], taps=taps, pad=pad,
+                tau_g=oracle.jitter(r["tau"], taps, pad),
+                flip_g=oracle.jitter(r["flip_mass"], taps, pad), n_boundary=r["n_boundary"])

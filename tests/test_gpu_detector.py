@@ -51,6 +51,21 @@ def test_jitter_kernel_matches_oracle():
         H.check_bins(out.cpu().numpy().astype(np.float64), ref, rel=1e-6, what="jitter")
 
 
+def test_jitter_replicate_matches_oracle():
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(15)
+    for traces, B, fwhm, dt in [(11, 512, 60e-12, 8e-12), (3, 3001, 70e-12, 4e-12),
+                                (2, 8, 200e-12, 8e-12), (4, 1, 60e-12, 8e-12)]:
+        x = rng.random((traces, B)).astype(np.float32)
+        xin = torch.from_numpy(x).cuda()
+        out = torch.empty_like(xin)
+        nlos.jitter(xin, out, traces, B, fwhm, dt, padding="replicate")
+        torch.cuda.synchronize()
+        ref = oracle.jitter(x.astype(np.float64), oracle.jitter_taps(fwhm, dt), "replicate")
+        H.check_bins(out.cpu().numpy().astype(np.float64), ref, rel=1e-6, what="jitter replicate")
+
+
 def test_reduce_matches_fp64():
     H.lib()
     from paper_2506_03747_gb300 import nlos

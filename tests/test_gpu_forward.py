@@ -40,7 +40,7 @@ def _compare(params, pts, s_begin=0, s_count=None, exact_flips=True, threads=0,
     assert abs(e_tot_g - e_tot_o) <= H.REL_ENERGY * e_tot_o + allow_e.sum()
     if exact_flips:
         tau_fc, nflip, du = H.flip_corrected_oracle(params, pts, g["scene"], s_begin, s_count)
-        tau_fc_g = oracle.jitter(tau_fc, o["taps"])
+        tau_fc_g = oracle.jitter(tau_fc, o["taps"], o["pad"])
         res["bin_err_exact"] = H.check_bins(g["tau"][sl], tau_fc_g, what="tau_G (flips moved)")
         res["energy_err_exact"] = H.check_energy(g["energy"][sl], tau_fc_g.sum(axis=1),
                                                  rel=rel_energy, what="energy (flips moved)")
@@ -86,6 +86,24 @@ def test_window_split_and_unaligned_bins():
                                    standoff_m=0.1, standoff_mode="euclidean")
     r = _compare(params, pts, rel_energy=1e-5)
     print("window split", r)
+
+
+@pytest.mark.parametrize("B", [2501, 700])
+def test_replicate_padding(B):
+    """Jitter with the edge bins continued outside the window: the window
+    starts inside the scene (bin 0 populated) and ends inside it (the last bin
+    populated), with one window (700 bins) and several (2501, not a multiple
+    of 4)."""
+    rng = np.random.default_rng(11)
+    pts = scenes.random_points(rng, 901, half=0.5, z_lo=0.2, z_hi=1.8)
+    params = scenes.default_params(scan_nx=9, scan_ny=7, wall_half_x=0.5, wall_half_y=0.5,
+                                   bin_width_s=2e-12, num_bins=B, jitter_fwhm_s=30e-12,
+                                   standoff_m=0.1, standoff_mode="euclidean",
+                                   window_start_m=1.2, jitter_padding="replicate")
+    g = H.gpu_forward(params, pts)
+    assert g["tau"][:, 0].any() and g["tau"][:, -1].any()
+    r = _compare(params, pts, rel_energy=1e-5)
+    print("replicate", B, r)
 
 
 def test_workload_union64_full_cube():
