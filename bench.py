@@ -335,12 +335,74 @@ def run_ours(args):
         line["splat_adjoint"] = splat_adjoint_bench(args.splat_steps, 1)
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         line["serving"] = serving_bench(args.serving_requests, args.serving_rate)
+    if rank == 0 and ws == 1 and args.lct_steps > 0:
+        line["lct"] = lct_bench(args.lct_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     scene.destroy()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def lct_bench(steps: int):
+    """The paper's FFT forward model on its dataset shape (128 x 128 depth map,
+    1024 bins of 32 ps, 2 m wall) against the direct pair sum of Eq. 1 on the
+    same surface (one point per pixel at its depth-bin centre, no cosines,
+    window from the wall). Reports both times and the shape correlation."""
+    import torch
+    from paper_2506_03747_gb300 import nlos
+    n, m, dt, w = 128, 1024, 32e-12, 1.0
+    cdt2 = 299792458.0 * dt / 2
+    rng = np.random.default_rng(0x4E4C4F53 + 9)
+    xs = -w + (np.arange(n) + 0.5) * (2 * w / n)
+    X, Y = np.meshgrid(xs, xs, indexing="ij")
+    z = 0.8 + 0.3 * np.exp(-((X - 0.2) ** 2 + Y ** 2) / 0.1) + 0.1 * X
+    depth = np.clip(np.rint(z / cdt2 - 1).astype(np.int32), 0, m - 1)
+    albedo = (0.2 + 0.8 * rng.beta(2, 2, size=(n, n))).astype(np.float32)
+    d_dev = torch.from_numpy(depth).cuda()
+    a_dev = torch.from_numpy(albedo).cuda()
+    tau = torch.empty((n, n, m), dtype=torch.float32, device="cuda")
+    plan = nlos.Lct(n, m, w, dt)
+    for _ in range(2):
+        plan.forward(d_dev, a_dev, tau)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        a.record()
+        plan.forward(d_dev, a_dev, tau)
+        b.record()
+    torch.cuda.synchronize()
+    lct_ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    lct_tau = tau.cpu().numpy()
+    plan.destroy()
+    # the same surface through the direct sum
+    pts = np.zeros((n * n, 8), np.float32)
+    pts[:, 0], pts[:, 1], pts[:, 2] = X.ravel(), Y.ravel(), ((depth + 1) * cdt2).ravel()
+    pts[:, 5], pts[:, 6], pts[:, 7] = -1.0, albedo.ravel(), (2 * w / n) ** 2
+    prm = nlos.params(scan_nx=n, scan_ny=n, wall_half_x=w, wall_half_y=w, bin_width_s=dt,
+                      num_bins=m, window_start_m=0.0, cos_mode="none")
+    sc = nlos.scene_create(prm, torch.from_numpy(pts).cuda())
+    dtau = torch.empty((n * n, m), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        nlos.forward(sc, dtau)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record()
+        nlos.forward(sc, dtau)
+        b.record()
+    torch.cuda.synchronize()
+    direct_ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    d_tau = dtau.cpu().numpy().reshape(n, n, m).transpose(1, 0, 2)  # scan order is y-major
+    sc.destroy()
+    u, v = lct_tau.ravel().astype(np.float64), d_tau.ravel().astype(np.float64)
+    corr = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
+    return {"workload": "128 x 128 depth map (Gaussian bump on a tilted plane at 0.7-1.2 m), "
+                        "1024 bins x 32 ps, 2 m wall, Beta(2,2) albedo",
+            "grid": [2 * n, 2 * n, 2 * m], "lct_forward_ms": lct_ms,
+            "direct_forward_ms": direct_ms, "direct_pairs": n * n * n * n,
+            "shape_correlation_lct_vs_direct": corr}
 
 
 def splat_adjoint_bench(steps: int, warmup: int):
@@ -525,6 +587,8 @@ def main():
                     help="scan points in the CPU baseline sample")
     ap.add_argument("--splat-steps", type=int, default=2,
                     help="steps of the differentiable-path measurement (0: skip)")
+    ap.add_argument("--lct-steps", type=int, default=3,
+                    help="timed passes of the FFT forward model comparison (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests in the serving replay (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=200.0,

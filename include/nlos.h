@@ -268,6 +268,34 @@ nlos_status nlos_philox(const uint32_t* ctr_dev, uint64_t n, uint32_t key0, uint
 nlos_status nlos_pair_table(nlos_scene* scene, uint64_t s_begin, uint64_t s_count, float* u_dev,
                             float* w_dev, void* cuda_stream);
 
+/* ---- The paper's FFT forward model (light-cone transform convolution) ---- */
+
+typedef struct nlos_lct nlos_lct;
+
+/* Plan of the paper's FFT forward model (the Theory section's 3-D convolution
+ * tau = R_t^{-1} F^{-1}[F(R_z V) . F(PSF)], Algorithm 1 steps 1.1-2.2) for an
+ * n x n confocal depth map over a wall of half side wall_half_m, with m time
+ * bins of bin_width_s (n, m powers of two; n <= 1024, m <= 4096). Computes the
+ * PSF (one node per lateral column, slope = w / (m c dt)) and its 3-D FFT on
+ * the zero-padded (2n) x (2n) x (2m) grid; holds two complex FP64 volumes of
+ * that size on the device (32 n^2 m bytes each). Synchronous. */
+nlos_status nlos_lct_create(uint32_t n, uint32_t m, double wall_half_m, double bin_width_s,
+                            void* cuda_stream, nlos_lct** out);
+
+/* One forward pass (asynchronous on cuda_stream, FP64 inside):
+ *   depth_dev  [n][n] int32 device: depth bin of each pixel (out of [0, m):
+ *              no surface there);
+ *   albedo_dev [n][n] float32 device, nullable (NULL: 0.5, as Algorithm 1);
+ *   tau_dev    [n][n][m] float32 device, overwritten.
+ * Depth bin j (0-based) enters the squared-depth sample ceil((j+1)^2 / m) with
+ * weight albedo / ((j+1) m^2); time bin j reads squared-time sample
+ * ceil((j+1)^2 / m) times m / (j+1)^4. Calls on one plan must not overlap. */
+nlos_status nlos_lct_forward(nlos_lct* plan, const int32_t* depth_dev, const float* albedo_dev,
+                             float* tau_dev, void* cuda_stream);
+
+/* Waits for the device and frees the plan. */
+nlos_status nlos_lct_destroy(nlos_lct* plan);
+
 /* ---- Serving: continuous batching of simulation requests ---------------- */
 
 typedef struct nlos_server nlos_server;

@@ -131,6 +131,10 @@ def load(path: str | None = None):
                                       ctypes.POINTER(_U32)]),
             "nlos_server_inject": (S, [_P, ctypes.c_int]),
             "nlos_server_device_cycles": (S, [_P, ctypes.POINTER(_U64)]),
+            "nlos_lct_create": (S, [_U32, _U32, ctypes.c_double, ctypes.c_double, _P,
+                                    ctypes.POINTER(ctypes.c_void_p)]),
+            "nlos_lct_forward": (S, [_P, _P, _P, _P, _P]),
+            "nlos_lct_destroy": (S, [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -415,3 +419,31 @@ def server_destroy(server: Server):
 
 def jitter_sigma_bins(fwhm_s: float, bin_width_s: float) -> float:
     return fwhm_s / (2.0 * math.sqrt(2.0 * math.log(2.0)) * bin_width_s)
+
+
+class Lct:
+    """Owning handle of an ``nlos_lct`` plan (the paper's FFT forward model)."""
+
+    def __init__(self, n: int, m: int, wall_half_m: float, bin_width_s: float, stream=None):
+        h = ctypes.c_void_p()
+        _check(load().nlos_lct_create(n, m, float(wall_half_m), float(bin_width_s),
+                                      _stream(stream), ctypes.byref(h)))
+        self.handle, self.n, self.m = h.value, n, m
+
+    def forward(self, depth, albedo, tau, stream=None):
+        """depth [n, n] int32, albedo [n, n] float32 or None, tau [n, n, m] float32
+        (CUDA tensors)."""
+        _check(load().nlos_lct_forward(self.handle, _ptr(depth), _ptr(albedo), _ptr(tau),
+                                       _stream(stream)))
+
+    def destroy(self):
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(load().nlos_lct_destroy(h))
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
