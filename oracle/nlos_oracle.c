@@ -285,7 +285,12 @@ static float stream_uniform(orc_stream* st) {
  *  - lambda < 30: Knuth's multiplication method in single precision (multiply
  *    uniforms until the product drops to expf(-lambda) or below; the count is
  *    the number of factors minus one);
- *  - lambda >= 30: PTRS, the transformed rejection method with squeeze of
+ *  - 30 <= lambda < 150: the sum of n = ceil(lambda / 30) Knuth draws of
+ *    mean lambda / n (single precision, drawn one after the other from the
+ *    same stream); a sum of independent Poisson variables is Poisson with
+ *    the summed mean, so this is exact and keeps the device off double
+ *    precision for the counts near a 100-photon peak;
+ *  - lambda >= 150: PTRS, the transformed rejection method with squeeze of
  *    W. Hoermann, "The transformed rejection method for generating Poisson
  *    random variables", Insurance: Mathematics and Economics 12 (1993),
  *    evaluated in double (log and lgamma of double agree to about the last
@@ -331,7 +336,15 @@ uint32_t orc_poisson_one(float lam, uint64_t index, uint64_t seed, uint32_t stre
   if (!(lam > 0.0f)) return 0u;
   orc_stream st;
   stream_init(&st, index, seed, stream_tag);
-  return lam < 30.0f ? poisson_knuth(lam, &st) : poisson_ptrs(lam, &st);
+  if (lam < 30.0f) return poisson_knuth(lam, &st);
+  if (lam < 150.0f) {
+    const float parts = ceilf(lam / 30.0f);
+    const float sub = lam / parts;
+    uint32_t k = 0;
+    for (int i = 0; i < (int)parts; ++i) k += poisson_knuth(sub, &st);
+    return k;
+  }
+  return poisson_ptrs(lam, &st);
 }
 
 void orc_poisson(const float* lam, int64_t n, uint64_t index_base, uint64_t seed,

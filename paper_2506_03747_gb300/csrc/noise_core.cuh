@@ -17,13 +17,17 @@ namespace nlos {
 // Per-bin stream: key = (seed_lo, seed_hi), counter = (index_lo, index_hi,
 // block, stream_tag); a word w gives the uniform ((w >> 9) + 0.5) * 2^-23.
 //  * lambda < 30: Knuth's multiplication method against expf(-lambda);
-//  * lambda >= 30: Hoermann's PTRS (1993), transformed rejection with squeeze,
-//    in double.
+//  * 30 <= lambda < 150: the sum of ceil(lambda / 30) Knuth draws of mean
+//    lambda / ceil(lambda / 30), one after the other from the same stream
+//    (exact: a sum of independent Poisson variables is Poisson);
+//  * lambda >= 150: Hoermann's PTRS (1993), transformed rejection with
+//    squeeze, in double.
 // ---------------------------------------------------------------------------
-// Both samplers are exact; the switch point only moves work between Knuth's
-// single-precision products and the PTRS branch, which runs in FP64 (slow on
-// this part), so it sits where PTRS becomes cheaper than ~lambda products.
+// All three are exact; the split only moves work between Knuth's single-
+// precision products (about lambda of them) and the PTRS branch, which runs
+// in FP64 (64 times slower per instruction on this part than FP32).
 constexpr float kKnuthMax = 30.0f;
+constexpr float kSplitMax = 150.0f;
 
 struct BinStream {
   uint4 ctr;
@@ -90,7 +94,15 @@ __device__ __forceinline__ uint32_t poisson_sample(float lam, uint64_t index, ui
                                                    uint32_t tag) {
   if (!(lam > 0.0f)) return 0u;
   BinStream st(index, seed, tag);
-  return lam < kKnuthMax ? poisson_knuth(lam, st) : poisson_ptrs(lam, st);
+  if (lam < kKnuthMax) return poisson_knuth(lam, st);
+  if (lam < kSplitMax) {
+    const float parts = ceilf(__fdiv_rn(lam, kKnuthMax));
+    const float sub = __fdiv_rn(lam, parts);
+    uint32_t k = 0;
+    for (int i = 0; i < (int)parts; ++i) k += poisson_knuth(sub, st);
+    return k;
+  }
+  return poisson_ptrs(lam, st);
 }
 
 
