@@ -166,8 +166,6 @@ int jitter_radius(double sigma);
 // Spatial ordering, packing and block bounds of a scene's points (order.cu):
 // the device counting sort, then the pack and bounds kernels, on stream st.
 cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st);
-// The same ordering on the host (serving uploads): out[P][8] = pts in order.
-void order_points_host(const float* pts, uint64_t P, float* out);
 // Tile bounds from a scan table (host).
 void tile_bounds_host(const ScanPoint* sp, uint64_t S, std::vector<TileBound>& out);
 

@@ -8,13 +8,15 @@
 // of the surface. The sum over points does not depend on the order; only the
 // FP32 rounding of the histogram accumulation does.
 //
-// Device steps (one stream, no host synchronisation):
+// Device steps (one stream, no host synchronisation; the step routines are
+// in order_core.cuh, shared with the serving kernel):
 //   1. box: the points' bounding box (order-preserving integer atomics),
 //   2. cell: each point's cell and the cell counts,
 //   3. scan: exclusive prefix sum of the counts (one CTA),
 //   4. scatter: perm[slot] = point, slot from the cell's cursor,
 //   5. pack (pack_pair through perm) and block bounds (one warp per block).
 #include "common.cuh"
+#include "order_core.cuh"
 #include "pack_core.cuh"
 
 #include <algorithm>
@@ -25,134 +27,27 @@ namespace nlos {
 
 namespace {
 
-
-// float -> unsigned with the same order
-__host__ __device__ inline uint32_t ord_bits(float f) {
-  uint32_t b;
-  memcpy(&b, &f, 4);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__host__ __device__ inline float ord_float(uint32_t u) {
-  const uint32_t b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
-  float f;
-  memcpy(&f, &b, 4);
-  return f;
-}
-
-__host__ __device__ inline uint32_t spread5(uint32_t v) {
-  uint32_t o = 0;
-  for (int b = 0; b < 5; ++b) o |= ((v >> b) & 1u) << (3 * b);
-  return o;
-}
-
-__host__ __device__ inline uint32_t cell_of(float x, float y, float z, const float* lo,
-                                            const float* inv) {
-  const float v[3] = {x, y, z};
-  uint32_t q[3];
-  for (int c = 0; c < 3; ++c) {
-    const float t = (v[c] - lo[c]) * inv[c];
-    q[c] = t > 0.f ? (uint32_t)fminf(t, 31.f) : 0u;
-  }
-  return spread5(q[0]) | (spread5(q[1]) << 1) | (spread5(q[2]) << 2);
-}
-
-__host__ __device__ inline void box_scale(const float* lo, const float* hi, float* inv) {
-  for (int c = 0; c < 3; ++c) {
-    const float ext = hi[c] - lo[c];
-    inv[c] = ext > 0.f ? 32.0f / ext : 0.f;
-  }
-}
-
 __global__ void __launch_bounds__(256) box_kernel(const float* __restrict__ raw, uint64_t P,
                                                   uint32_t* box) {
-  uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    for (int c = 0; c < 3; ++c) {
-      const uint32_t u = ord_bits(raw[8 * i + c]);
-      mn[c] = min(mn[c], u);
-      mx[c] = max(mx[c], u);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1)
-    for (int c = 0; c < 3; ++c) {
-      mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
-      mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
-    }
-  // CTA reduction first: one global atomic per CTA and word (same-address
-  // atomics from every warp serialise)
-  __shared__ uint32_t s[8][6];
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0)
-    for (int c = 0; c < 3; ++c) {
-      s[w][c] = mn[c];
-      s[w][3 + c] = mx[c];
-    }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    const int c = threadIdx.x;
-    uint32_t v = s[0][c];
-    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) v = c < 3 ? min(v, s[j][c]) : max(v, s[j][c]);
-    if (c < 3) atomicMin(&box[c], v);
-    else atomicMax(&box[c], v);
-  }
+  __shared__ uint32_t red[8 * 6];
+  box_range(raw, 0, P, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+            (uint64_t)gridDim.x * blockDim.x, box, red);
 }
 
 __global__ void cell_kernel(const float* __restrict__ raw, uint64_t P, const uint32_t* box,
                             uint16_t* cell, uint32_t* counts) {
-  float lo[3], hi[3], inv[3];
-  for (int c = 0; c < 3; ++c) {
-    lo[c] = ord_float(box[c]);
-    hi[c] = ord_float(box[3 + c]);
-  }
-  box_scale(lo, hi, inv);
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = cell_of(raw[8 * i], raw[8 * i + 1], raw[8 * i + 2], lo, inv);
-    cell[i] = (uint16_t)k;
-    atomicAdd(&counts[k], 1u);
-  }
+  cell_range(raw, 0, P, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+             (uint64_t)gridDim.x * blockDim.x, box, cell, counts);
 }
 
-// One CTA of 1024 threads: counts[c] <- sum of counts[0..c). Warp w scans
-// cells [w * 1024, (w + 1) * 1024) 32 at a time (coalesced loads, shuffle
-// scans), then the 32 warp totals are scanned.
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* counts) {
-  constexpr int kPerWarp = kOrderCells / 32;
   __shared__ uint32_t wsum[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* seg = counts + (size_t)w * kPerWarp;
-  uint32_t carry = 0;
-  for (int j = 0; j < kPerWarp; j += 32) {
-    const uint32_t v = seg[j + lane];
-    uint32_t x = v;  // inclusive scan of the 32 values
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    seg[j + lane] = carry + x - v;  // exclusive within the warp's segment
-    carry += __shfl_sync(0xffffffffu, x, 31);
-  }
-  if (lane == 0) wsum[w] = carry;
-  __syncthreads();
-  if (w == 0) {
-    const uint32_t v = wsum[lane];
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    wsum[lane] = x - v;
-  }
-  __syncthreads();
-  const uint32_t base = wsum[w];
-  for (int j = lane; j < kPerWarp; j += 32) seg[j] += base;
+  scan_cells(counts, wsum);
 }
 
 __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* cursor, uint32_t* perm) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    perm[atomicAdd(&cursor[cell[i]], 1u)] = (uint32_t)i;
+  scatter_range(cell, 0, P, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                (uint64_t)gridDim.x * blockDim.x, cursor, perm);
 }
 
 __global__ void pack_perm_kernel(const float* __restrict__ raw, uint64_t P, int scan_mode,
@@ -205,29 +100,6 @@ cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st) {
   bounds_kernel<<<grid_for(n_sub, 8, s.num_sms), 256, 0, st>>>(
       s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.bounds, n_sub);
   return cudaGetLastError();
-}
-
-void order_points_host(const float* pts, uint64_t P, float* out) {
-  if (P == 0) return;
-  float lo[3], hi[3], inv[3];
-  for (int c = 0; c < 3; ++c) lo[c] = hi[c] = pts[c];
-  for (uint64_t i = 1; i < P; ++i)
-    for (int c = 0; c < 3; ++c) {
-      lo[c] = std::min(lo[c], pts[8 * i + c]);
-      hi[c] = std::max(hi[c], pts[8 * i + c]);
-    }
-  box_scale(lo, hi, inv);
-  std::vector<uint32_t> start(kOrderCells + 1, 0);
-  std::vector<uint16_t> cell(P);
-  for (uint64_t i = 0; i < P; ++i) {
-    cell[i] = (uint16_t)cell_of(pts[8 * i], pts[8 * i + 1], pts[8 * i + 2], lo, inv);
-    ++start[cell[i] + 1];
-  }
-  for (uint32_t c = 0; c < kOrderCells; ++c) start[c + 1] += start[c];
-  for (uint64_t i = 0; i < P; ++i) {
-    const uint32_t slot = start[cell[i]]++;
-    std::copy(pts + 8 * i, pts + 8 * i + 8, out + 8 * (uint64_t)slot);
-  }
 }
 
 void tile_bounds_host(const ScanPoint* sp, uint64_t S, std::vector<TileBound>& out) {

@@ -4,7 +4,11 @@
 // thread admits them first-in first-out while the device memory they hold
 // stays within the HBM budget, uploads their points and scan tables on a copy
 // stream, and publishes their work as items in a ring in mapped host memory:
-//   PREP    pack the points (ingest step) and zero the output cube,
+//   BOX, CELL, SCAN, SCATTER  the spatial ordering of the points (a counting
+//           sort by Morton cell: bounding box, cells and counts, prefix sum,
+//           permutation), the same steps as the standalone scene's ordering,
+//   PREP    pack the points in that order (ingest step) with the block
+//           bounds, and zero the output cube,
 //   FORWARD pair-histogram units (scan tile, bin window, point block) with the
 //           fused jitter, exactly as the standalone forward kernel runs them,
 //   REDUCE  per-cube maximum and FP64 sums,
@@ -25,6 +29,7 @@
 #include "device_util.cuh"
 #include "forward_core.cuh"
 #include "noise_core.cuh"
+#include "order_core.cuh"
 #include "pack_core.cuh"
 
 #include <algorithm>
@@ -50,10 +55,17 @@ void scan_points_host(const nlos_params& p, const Geometry& g, std::vector<ScanP
 
 namespace serve {
 
-enum ItemKind : uint32_t { K_PACK = 0, K_ZERO = 1, K_FWD = 2, K_REDUCE = 3, K_NOISE = 4 };
-enum Phase : int { PH_PREP = 0, PH_FWD = 1, PH_REDUCE = 2, PH_NOISE = 3 };
+enum ItemKind : uint32_t {
+  K_BOX = 0, K_CELL = 1, K_SCAN = 2, K_SCATTER = 3, K_PACK = 4, K_ZERO = 5, K_FWD = 6,
+  K_REDUCE = 7, K_NOISE = 8
+};
+enum Phase : int {
+  PH_BOX = 0, PH_CELL = 1, PH_SCAN = 2, PH_SCATTER = 3, PH_PREP = 4, PH_FWD = 5, PH_REDUCE = 6,
+  PH_NOISE = 7
+};
+constexpr int kPhases = 8;
 __host__ __device__ inline int phase_of(uint32_t kind) {
-  return kind <= K_ZERO ? PH_PREP : kind == K_FWD ? PH_FWD : kind == K_REDUCE ? PH_REDUCE : PH_NOISE;
+  return kind <= K_SCATTER ? (int)kind : kind <= K_ZERO ? PH_PREP : (int)kind - 1;
 }
 
 constexpr uint64_t kRing = 1ull << 16;      // work-item ring slots
@@ -75,6 +87,7 @@ constexpr uint32_t kServePpb = NLOS_SERVE_PPB; // pairs per staged point block
 constexpr uint32_t kPackChunk = 2048;        // pairs per PACK item (a multiple of kSubPairs)
 static_assert(kPackChunk % kSubPairs == 0, "pack items start on sub-block edges");
 constexpr uint64_t kZeroChunk = 1ull << 16;  // floats per ZERO item
+constexpr uint64_t kOrderChunk = 1ull << 16; // points per BOX / CELL / SCATTER item
 constexpr uint32_t kFwdChunk = NLOS_SERVE_FWD_CHUNK;  // point blocks per FORWARD item
 constexpr uint64_t kWindowPerSm = 16;        // items outstanding per SM (publication window)
 constexpr uint64_t kMaxPhaseItems = 16384;   // FORWARD items per request (coarser beyond)
@@ -88,7 +101,10 @@ constexpr uint64_t kSkip = ~0ull - 1;
 
 struct __align__(16) JobDesc {
   FwdArgs fwd;               // forward arguments (tau, pairs, scan, taps, ...)
-  const float* raw;          // [P][8] uploaded points
+  const float* raw;          // [P][8] uploaded points (submission order)
+  uint32_t* perm;            // [P] packed position -> point (ordering result)
+  uint16_t* cell;            // [P] Morton cell of each point
+  uint32_t* cells;           // [kOrderCells] counts / cursors, then the box words
   uint32_t* counts;          // [S][B] or null
   SceneScratch* scratch;     // device
   uint64_t P, S, n;          // points, scan points, bins in the cube
@@ -124,7 +140,7 @@ struct Control {
 };
 
 struct JobStatus {
-  uint32_t done[4];    // items finished per phase
+  uint32_t done[kPhases];  // items finished per phase
 };
 
 struct ServeArgs {
@@ -229,11 +245,11 @@ __device__ __noinline__ void noise_item(const JobDesc& j, uint64_t b, uint64_t e
 __device__ __noinline__ void pack_item(const JobDesc& j, uint64_t b, uint64_t e) {
   for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x)
     pack_pair(j.raw, j.P, k, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt,
-              const_cast<PointPair*>(j.fwd.pairs), &j.scratch->err);
+              const_cast<PointPair*>(j.fwd.pairs), &j.scratch->err, j.perm);
   // bounds of the sub-blocks this item packs (items start on sub-block edges)
   const uint64_t sb_end = (e + kSubPairs - 1) / kSubPairs;
   for (uint64_t sb = b / kSubPairs + (threadIdx.x >> 5); sb < sb_end; sb += blockDim.x >> 5)
-    block_bound_warp(j.raw, j.P, sb, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt, nullptr,
+    block_bound_warp(j.raw, j.P, sb, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt, j.perm,
                      const_cast<BlockBound*>(j.fwd.bounds) + sb);
 }
 
@@ -342,6 +358,20 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       __syncthreads();
     }
     switch (item.kind) {
+      case K_BOX:  // the histogram's shared memory is free between forward items
+        box_range(jd->raw, item.begin, item.end, tid, blockDim.x, jd->cells + kOrderCells,
+                  reinterpret_cast<uint32_t*>(sm.hist));
+        break;
+      case K_CELL:
+        cell_range(jd->raw, item.begin, item.end, tid, blockDim.x, jd->cells + kOrderCells,
+                   jd->cell, jd->cells);
+        break;
+      case K_SCAN:
+        scan_cells(jd->cells, reinterpret_cast<uint32_t*>(sm.hist));
+        break;
+      case K_SCATTER:
+        scatter_range(jd->cell, item.begin, item.end, tid, blockDim.x, jd->cells, jd->perm);
+        break;
       case K_PACK:
         pack_item(*jd, item.begin, item.end);
         break;
@@ -407,6 +437,9 @@ struct Request {
   size_t bytes = 0;
   PointPair* pairs = nullptr;
   float* raw = nullptr;
+  uint32_t* perm = nullptr;
+  uint16_t* cell = nullptr;
+  uint32_t* cells = nullptr;
   ScanPoint* scan = nullptr;
   float* tau = nullptr;
   uint32_t* counts = nullptr;
@@ -418,14 +451,14 @@ struct Request {
   std::atomic<int> upload{0};  // 0 queued, 1 copies issued (ev recorded), 2 failed
   std::string upload_msg;
   int phase = 0;
-  uint32_t items[4] = {0, 0, 0, 0};
+  uint32_t items[kPhases] = {};
   uint32_t withheld = 0;  // published items that will never complete (fault injection)
   std::vector<WorkItem> backlog;  // items of the current phase not yet published
   size_t backlog_pos = 0;
   uint64_t first_item = 0, last_item = 0;
   bool release_on_done = false;
   Clock::time_point t_submit, t_done;
-  Clock::time_point t_mark[8];  // tracing: admit, upload done, phase 0..3 done, finish
+  Clock::time_point t_mark[2 + kPhases];  // tracing: admit, upload done, each phase done
   uint32_t items_total = 0;
   nlos_stats stats{};
 };
@@ -484,6 +517,9 @@ void carve(Request* r) {
   };
   size_t o_pairs = take(sizeof(PointPair) * (n_pairs ? n_pairs : 1));
   size_t o_raw = take(sizeof(float) * 8 * (g.P ? g.P : 1));
+  size_t o_perm = take(sizeof(uint32_t) * (g.P ? g.P : 1));
+  size_t o_cell = take(sizeof(uint16_t) * (g.P ? g.P : 1));
+  size_t o_cells = take(sizeof(uint32_t) * (kOrderCells + kOrderBoxWords));
   size_t o_scan = take(sizeof(ScanPoint) * g.S);
   size_t o_tau = take(sizeof(float) * g.S * g.B);
   size_t o_cnt = g.noise_mode != NLOS_NOISE_NONE ? take(sizeof(uint32_t) * g.S * g.B) : 0;
@@ -495,6 +531,9 @@ void carve(Request* r) {
   if (!r->dev) return;
   r->pairs = reinterpret_cast<PointPair*>(r->dev + o_pairs);
   r->raw = reinterpret_cast<float*>(r->dev + o_raw);
+  r->perm = reinterpret_cast<uint32_t*>(r->dev + o_perm);
+  r->cell = reinterpret_cast<uint16_t*>(r->dev + o_cell);
+  r->cells = reinterpret_cast<uint32_t*>(r->dev + o_cells);
   r->scan = reinterpret_cast<ScanPoint*>(r->dev + o_scan);
   r->tau = reinterpret_cast<float*>(r->dev + o_tau);
   r->counts = g.noise_mode != NLOS_NOISE_NONE ? reinterpret_cast<uint32_t*>(r->dev + o_cnt) : nullptr;
@@ -542,6 +581,9 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
     if (a.replicate) jitter_tails(a.taps, a.R, a.tail);
   }
   j.raw = r->raw;
+  j.perm = r->perm;
+  j.cell = r->cell;
+  j.cells = r->cells;
   j.counts = r->counts;
   j.scratch = r->scratch;
   j.P = g.P;
@@ -622,7 +664,14 @@ void publish_phase(Server& sv, Request* r, int phase) {
   std::vector<WorkItem> items;
   const uint16_t job = (uint16_t)r->slot;
   const uint32_t gen = (uint32_t)r->ticket;
-  if (phase == PH_PREP) {
+  if (phase >= PH_BOX && phase <= PH_SCATTER) {
+    if (phase == PH_SCAN) {
+      if (g.P) items.push_back({job, K_SCAN, gen, 0, 0, 0});
+    } else {
+      for (uint64_t b = 0; b < g.P; b += kOrderChunk)
+        items.push_back({job, (uint16_t)phase, gen, b, std::min<uint64_t>(g.P, b + kOrderChunk), 0});
+    }
+  } else if (phase == PH_PREP) {
     const uint64_t n_pairs = (g.P + 1) / 2;
     for (uint64_t b = 0; b < n_pairs; b += kPackChunk)
       items.push_back({job, K_PACK, gen, b, std::min<uint64_t>(n_pairs, b + kPackChunk), 0});
@@ -664,12 +713,14 @@ void trace_request(Server& sv, Request* r) {
   };
   std::fprintf(sv.trace,
                "{\"ticket\": %llu, \"S\": %llu, \"B\": %u, \"P\": %llu, \"items\": %u, "
-               "\"status\": %d, \"admit\": %.3f, \"uploaded\": %.3f, \"prep\": %.3f, "
-               "\"forward\": %.3f, \"reduce\": %.3f, \"noise\": %.3f, \"done\": %.3f}\n",
+               "\"status\": %d, \"admit\": %.3f, \"uploaded\": %.3f, \"ordered\": %.3f, "
+               "\"prep\": %.3f, \"forward\": %.3f, \"reduce\": %.3f, \"noise\": %.3f, "
+               "\"done\": %.3f}\n",
                (unsigned long long)r->ticket, (unsigned long long)r->g.S, r->g.B,
                (unsigned long long)r->g.P, r->items_total, (int)r->status, ms(r->t_mark[0]),
-               ms(r->t_mark[1]), ms(r->t_mark[2]), ms(r->t_mark[3]), ms(r->t_mark[4]),
-               ms(r->t_mark[5]), ms(r->t_done));
+               ms(r->t_mark[1]), ms(r->t_mark[2 + PH_SCATTER]), ms(r->t_mark[2 + PH_PREP]),
+               ms(r->t_mark[2 + PH_FWD]), ms(r->t_mark[2 + PH_REDUCE]),
+               ms(r->t_mark[2 + PH_NOISE]), ms(r->t_done));
   std::fflush(sv.trace);
 }
 
@@ -762,7 +813,7 @@ bool step(Server& sv) {
         std::atomic_thread_fence(std::memory_order_seq_cst);
         r->state = R_RUNNING;
         r->t_mark[1] = Clock::now();
-        publish_phase(sv, r, PH_PREP);
+        publish_phase(sv, r, PH_BOX);
         busy = true;
       }
     } else if (r->state == R_RUNNING) {
@@ -785,7 +836,7 @@ bool step(Server& sv) {
           r->t_mark[2 + r->phase] = Clock::now();
           r->items_total += r->items[r->phase];
           int next = r->phase + 1;
-          if (next == PH_NOISE && r->g.noise_mode == NLOS_NOISE_NONE) next = 4;
+          if (next == PH_NOISE && r->g.noise_mode == NLOS_NOISE_NONE) next = kPhases;
           if (next <= PH_NOISE) {
             publish_phase(sv, r, next);
           } else {
@@ -856,8 +907,9 @@ bool step(Server& sv) {
   return busy || !sv.active.empty();
 }
 
-// Uploader thread: scan table, points and a zeroed scratch of each admitted
-// request on the copy stream, then the request's event.
+// Uploader thread: scan table, tile bounds, points, a zeroed scratch and the
+// ordering's initial counts and box of each admitted request on the copy
+// stream, then the request's event.
 void upload_loop(Server* sv) {
   cudaSetDevice(sv->device);
   for (;;) {
@@ -873,18 +925,22 @@ void upload_loop(Server* sv) {
     nlos::scan_points_host(r->params, r->g, hs);
     std::vector<TileBound> ht;
     nlos::tile_bounds_host(hs.data(), r->g.S, ht);
-    // the points in the spatial order the forward's unit culling relies on
-    std::vector<float> ordered(r->pts.size());
-    nlos::order_points_host(r->pts.data(), r->g.P, ordered.data());
     SceneScratch zero{};
+    // min words all ones, max words zero (order-preserving bits)
+    static const uint32_t box0[kOrderBoxWords] = {~0u, ~0u, ~0u, 0u, 0u, 0u, 0u, 0u};
     cudaError_t e = cudaMemcpyAsync(r->scan, hs.data(), sizeof(ScanPoint) * r->g.S,
                                     cudaMemcpyHostToDevice, sv->cstream);
     if (e == cudaSuccess && !ht.empty())
       e = cudaMemcpyAsync(r->tiles, ht.data(), sizeof(TileBound) * ht.size(),
                           cudaMemcpyHostToDevice, sv->cstream);
     if (e == cudaSuccess && r->g.P)
-      e = cudaMemcpyAsync(r->raw, ordered.data(), sizeof(float) * 8 * r->g.P,
+      e = cudaMemcpyAsync(r->raw, r->pts.data(), sizeof(float) * 8 * r->g.P,
                           cudaMemcpyHostToDevice, sv->cstream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(r->cells, 0, sizeof(uint32_t) * kOrderCells, sv->cstream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(r->cells + kOrderCells, box0, sizeof(box0), cudaMemcpyHostToDevice,
+                          sv->cstream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->scratch, &zero, sizeof(zero), cudaMemcpyHostToDevice, sv->cstream);
     if (e == cudaSuccess) e = cudaEventRecord(r->ev, sv->cstream);
