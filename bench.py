@@ -536,6 +536,15 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
                 pending.discard(i)
         time.sleep(0.0002)
     th.join()
+    # SM cycles of the persistent kernel (posted when it exits, which it does
+    # once the server parks it with nothing left to run)
+    cyc, prev = None, None
+    for _ in range(100):
+        cyc = srv.device_cycles()
+        if cyc == prev and sum(cyc.values()) > 0:
+            break
+        prev = cyc
+        time.sleep(0.02)
     srv.destroy()
     lat_b = np.array([done_at[i] - (t0 + reqs[i]["arrival_s"]) for i in range(len(reqs))])
     span_b = max(done_at) - t0
@@ -570,7 +579,9 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
 
     return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "budget_gb": budget_gb,
             "offered_pairs_per_s": tot_pairs / reqs[-1]["arrival_s"],
-            "continuous_batching": summ(lat_b, span_b), "one_at_a_time": summ(lat_1, span_1),
+            "continuous_batching": dict(summ(lat_b, span_b), device_cycle_shares={
+                k: v / max(1, sum(cyc.values())) for k, v in cyc.items()}),
+            "one_at_a_time": summ(lat_1, span_1),
             "failures": failures[:5]}
 
 

@@ -711,8 +711,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // number beside it (kNoUnit ends the run); the full barrier orders that write
 // before the consumers read it. Units come either from the range [u0, u1)
 // (chunk_counter == nullptr) or in chunks of `chunk` units claimed from
-// *chunk_counter until units_total is reached, so that CTAs that meet cheap
-// units (most pairs stopped by the early out) take more of them. Consumers
+// *chunk_counter until units_total is reached (or, with max_claims > 0, after
+// that many claims), so that CTAs that meet cheap units (culled, or most
+// pairs stopped by the early out) take more of them. Consumers
 // flush their (tile, window) histogram whenever the tile changes and at the
 // end. `it` carries the barrier phases across calls (the serving kernel runs
 // one call per work item). Every wait is bounded; returns false if one gave
@@ -721,7 +722,8 @@ template <int SCAN, int COS, int MODE>
 __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
                            const FwdSmem& sm, int stages, FwdCount& cnt, const MomTab* mt,
                            uint32_t& it, unsigned long long* chunk_counter = nullptr,
-                           unsigned long long chunk = 0, unsigned long long units_total = 0) {
+                           unsigned long long chunk = 0, unsigned long long units_total = 0,
+                           uint32_t max_claims = 0) {
   const int mom_J = (MODE == MODE_SPLAT_MOM) ? mt->J : 0;
   const uint32_t hist_words = (MODE == MODE_SPLAT_MOM) ? (uint32_t)kMoments * kMomRows * kTile
                                                        : a.bw * kTile;
@@ -747,27 +749,33 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     const bool cull = NLOS_FWD_CULL && a.bounds != nullptr && MODE != MODE_NEAREST_COUNT;
     const float margin = window_margin<MODE>(a, mom_J);
     unsigned long long cur = u0, lim = u1, next = 0;
+    bool have_next = false;  // a chunk claimed ahead of its use
+    uint32_t claims = 0;
+    auto claim = [&]() {
+      unsigned long long c = 0;
+      if (lane == 0) c = atomicAdd(chunk_counter, 1ull);
+      ++claims;
+      return __shfl_sync(0xffffffffu, c, 0);
+    };
     if (chunk_counter) {
-      unsigned long long c = 0, n2 = 0;
-      if (lane == 0) {
-        c = atomicAdd(chunk_counter, 1ull);
-        n2 = atomicAdd(chunk_counter, 1ull);
-      }
-      c = __shfl_sync(0xffffffffu, c, 0);
-      next = __shfl_sync(0xffffffffu, n2, 0);
+      const unsigned long long c = claim();
       cur = min(c * chunk, units_total);
       lim = min(cur + chunk, units_total);
+      if (cur < lim && (max_claims == 0 || claims < max_claims)) {
+        next = claim();
+        have_next = true;
+      }
     }
     uint32_t k = 0;
     bool failed = false;
     for (;;) {
-      if (cur == lim && chunk_counter && cur < units_total) {
+      if (cur == lim && have_next) {
         cur = min(next * chunk, units_total);
         lim = min(cur + chunk, units_total);
-        if (cur < lim) {
-          unsigned long long n2 = 0;
-          if (lane == 0) n2 = atomicAdd(chunk_counter, 1ull);
-          next = __shfl_sync(0xffffffffu, n2, 0);
+        have_next = false;
+        if (cur < lim && (max_claims == 0 || claims < max_claims)) {
+          next = claim();
+          have_next = true;
         }
       }
       if (cur >= lim) break;

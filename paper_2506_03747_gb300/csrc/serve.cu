@@ -15,12 +15,15 @@
 //   NOISE   Philox/Poisson counts.
 // The next phase of a request is published when the device reports the
 // current one complete. Requests admitted while others run are interleaved
-// item by item on the device.
+// item by item on the device. FORWARD items go to the main ring; the short
+// items of the other phases go to an express ring, which the device drains
+// first, so a request's small phases wait for at most about one running item
+// per SM instead of queueing behind the forward work published before them.
 //
 // Device side: one persistent kernel (one CTA per SM) claims items in order
-// from a device-side head counter once the host has published them (tail in
-// mapped memory), copies the item and its job descriptor into shared memory,
-// runs it and bumps the job's phase counter in mapped memory. Every wait is
+// from a device-side head counter per ring once the host has published them
+// (tails in mapped memory), copies the item and its job descriptor into
+// shared memory, runs it and bumps the job's phase counter in mapped memory. Every wait is
 // bounded: an unpublished claimed item gives up after about a second and sets
 // an error word; an idle CTA exits after the host parks the queue (or after
 // about a second with nothing to do), and the host relaunches the kernel when
@@ -46,7 +49,11 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <utility>
 #include <vector>
+#ifdef __linux__
+#include <sys/prctl.h>
+#endif
 
 namespace nlos {
 
@@ -68,16 +75,13 @@ __host__ __device__ inline int phase_of(uint32_t kind) {
   return kind <= K_SCATTER ? (int)kind : kind <= K_ZERO ? PH_PREP : (int)kind - 1;
 }
 
-constexpr uint64_t kRing = 1ull << 16;      // work-item ring slots
+constexpr uint64_t kRing = 1ull << 16;      // work-item slots per ring (main, express)
 constexpr int kMaxJobs = 1024;               // concurrently admitted requests
 #ifndef NLOS_SERVE_FWD_INLINE
 #define NLOS_SERVE_FWD_INLINE __forceinline__
 #endif
 #ifndef NLOS_SERVE_CAPBW
 #define NLOS_SERVE_CAPBW 1024
-#endif
-#ifndef NLOS_SERVE_FWD_CHUNK
-#define NLOS_SERVE_FWD_CHUNK 64
 #endif
 #ifndef NLOS_SERVE_PPB
 #define NLOS_SERVE_PPB 512
@@ -87,10 +91,20 @@ constexpr uint32_t kServePpb = NLOS_SERVE_PPB; // pairs per staged point block
 constexpr uint32_t kPackChunk = 2048;        // pairs per PACK item (a multiple of kSubPairs)
 static_assert(kPackChunk % kSubPairs == 0, "pack items start on sub-block edges");
 constexpr uint64_t kZeroChunk = 1ull << 16;  // floats per ZERO item
-constexpr uint64_t kOrderChunk = 1ull << 16; // points per BOX / CELL / SCATTER item
-constexpr uint32_t kFwdChunk = NLOS_SERVE_FWD_CHUNK;  // point blocks per FORWARD item
-constexpr uint64_t kWindowPerSm = 16;        // items outstanding per SM (publication window)
-constexpr uint64_t kMaxPhaseItems = 16384;   // FORWARD items per request (coarser beyond)
+constexpr uint64_t kOrderChunk = 1ull << 13; // points per BOX / CELL / SCATTER item
+// FORWARD: a request's units are split into about kFwdChunksPerSm chunks per
+// SM (as the standalone launch splits them), at most kFwdMaxChunk units each;
+// each FORWARD item claims up to kFwdClaims chunks from the request's
+// counter, so that CTAs meeting cheap (culled) units take more of them, and
+// a CTA keeps its histogram across the units of one (tile, window) of a
+// chunk. The cap bounds an item (128 units of 32 scan points x 1024 points,
+// about 1 ms at most), and with it how long express items can wait for a
+// CTA when every CTA has just started a FORWARD item.
+constexpr uint64_t kFwdChunksPerSm = 32;
+constexpr uint64_t kFwdMaxChunk = 128;
+constexpr uint32_t kFwdClaims = 4;
+constexpr uint64_t kWindowPerSm = 16;        // main-ring items outstanding per SM (publication window)
+constexpr uint64_t kXWindowPerSm = 32;       // express-ring items outstanding per SM
 constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
 constexpr uint64_t kNoiseChunk = 1ull << 13; // bins per NOISE item
 constexpr long long kIdleCycles = 2000000000LL;  // ~1 s without work: exit
@@ -126,13 +140,13 @@ struct __align__(32) WorkItem {
 static_assert(sizeof(WorkItem) == 32, "work item layout");
 
 struct Control {
-  uint64_t tail;       // items published (host)
-  uint64_t completed;  // items finished or skipped (device)
+  uint64_t tail[2];       // items published per ring (host): main, express
+  uint64_t completed[2];  // items finished or skipped per ring (device)
   uint64_t err_item;   // ring index of an item whose publication wait gave up
   uint32_t park;       // host: idle CTAs may exit
   uint32_t err;        // device: kErr* bits
   int32_t alive;       // device: CTAs running
-  uint32_t pad[7];
+  uint32_t pad[3];
   // device: SM cycles (summed over CTAs) spent waiting for or claiming work,
   // running FORWARD items, and running the other items
   unsigned long long cycles[3];
@@ -145,10 +159,10 @@ struct JobStatus {
 
 struct ServeArgs {
   Control* ctl;        // mapped
-  WorkItem* ring;      // mapped [kRing]
+  WorkItem* ring;      // mapped [2][kRing]: main, express
   JobDesc* jobs;       // mapped [kMaxJobs]
   JobStatus* status;   // mapped [kMaxJobs]
-  unsigned long long* head;  // device
+  unsigned long long* head;  // device [2]: next index to claim per ring
 };
 
 __device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t* p) {
@@ -163,39 +177,42 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
 
 // One instance per (scan, cosine, bin mode).
 template <int SCAN, int COS, int MODE>
-__device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, uint64_t b, uint64_t e,
-                                           const FwdSmem& sm, uint32_t& it) {
+__device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, const FwdSmem& sm,
+                                                    uint32_t& it) {
   FwdCount cnt;
-  const bool ok = fwd_run_ws<SCAN, COS, MODE>(a, b, e, sm, kServeStages, cnt, nullptr, it);
+  const bool ok = fwd_run_ws<SCAN, COS, MODE>(a, 0, 0, sm, kServeStages, cnt, nullptr, it,
+                                              a.next_chunk, a.chunk, a.units, kFwdClaims);
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
   if ((threadIdx.x & 31) == 0 && cnt.tested) atomicAdd(a.pairs_tested, cnt.tested * 64ull);
   return ok;
 }
 
 template <int SCAN, int COS>
-__device__ bool fwd_item_cos(const FwdArgs& a, uint64_t b, uint64_t e, const FwdSmem& sm,
-                             uint32_t& it, int bin_mode) {
-  return bin_mode == NLOS_BIN_SPLAT ? fwd_item_mode<SCAN, COS, MODE_SPLAT>(a, b, e, sm, it)
-                                    : fwd_item_mode<SCAN, COS, MODE_NEAREST>(a, b, e, sm, it);
+__device__ bool fwd_item_cos(const FwdArgs& a, const FwdSmem& sm, uint32_t& it, int bin_mode) {
+  return bin_mode == NLOS_BIN_SPLAT ? fwd_item_mode<SCAN, COS, MODE_SPLAT>(a, sm, it)
+                                    : fwd_item_mode<SCAN, COS, MODE_NEAREST>(a, sm, it);
 }
 
-__device__ bool fwd_item(const JobDesc& j, uint64_t b, uint64_t e, const FwdSmem& sm,
-                         uint32_t& it) {
+// FORWARD: up to kFwdClaims chunks of the job's units, claimed from its
+// counter (the item's range is unused).
+__device__ bool fwd_item(const JobDesc& j, const FwdSmem& sm, uint32_t& it) {
   const FwdArgs& a = j.fwd;
   const int m = j.bin_mode;
   if (j.scan_mode == NLOS_CONFOCAL) {
-    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, m);
-    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, m);
-    return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, m);
+    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_NONE>(a, sm, it, m);
+    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, sm, it, m);
+    return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, sm, it, m);
   }
-  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, b, e, sm, it, m);
-  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, b, e, sm, it, m);
-  return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, b, e, sm, it, m);
+  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, sm, it, m);
+  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, sm, it, m);
+  return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, sm, it, m);
 }
 
 // REDUCE: transients [b, e) of the job, one warp per transient; the cube's
-// maximum and FP64 sums go to the job's scratch.
-__device__ __noinline__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t e) {
+// maximum and FP64 sums go to the job's scratch, one atomic per item and
+// quantity (same-address atomics from every warp would serialise). red:
+// shared scratch of 3 doubles per warp.
+__device__ __noinline__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t e, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t B = j.fwd.B;
   double csum = 0.0, csq = 0.0;
@@ -221,9 +238,21 @@ __device__ __noinline__ void reduce_item(const JobDesc& j, uint64_t b, uint64_t 
     cmax = fmaxf(cmax, m);
   }
   if (lane == 0) {
-    atomicMax(&j.scratch->peak_bits, __float_as_uint(cmax));
-    atomicAdd(&j.scratch->sum, csum);
-    atomicAdd(&j.scratch->sumsq, csq);
+    red[warp] = csum;
+    red[nwarps + warp] = csq;
+    red[2 * nwarps + warp] = (double)cmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0, q = 0.0, m = 0.0;
+    for (int w = 0; w < nwarps; ++w) {
+      s += red[w];
+      q += red[nwarps + w];
+      m = fmax(m, red[2 * nwarps + w]);
+    }
+    atomicMax(&j.scratch->peak_bits, __float_as_uint((float)m));
+    atomicAdd(&j.scratch->sum, s);
+    atomicAdd(&j.scratch->sumsq, q);
   }
 }
 
@@ -273,6 +302,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
   JobDesc* jd = reinterpret_cast<JobDesc*>(sm.units + kServeStages + 1);
   __shared__ WorkItem s_item;
   __shared__ unsigned long long s_idx;
+  __shared__ int s_lane;  // ring of the claimed item
 
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -288,14 +318,29 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
 
   for (;;) {
     if (tid == 0) {
-      // claim the next published index: compare-and-swap on the device head
-      // against a cached tail (it only grows, so a stale value is a safe
-      // bound); the tail in host memory is read again only when the head
-      // has caught up with the cached value
+      // claim the next published index: express ring first (its tail is
+      // read from host memory on every pass: the ring is mostly empty, and a
+      // stale tail would hold its items back), then the main ring by
+      // compare-and-swap on the device head against a cached tail (it only
+      // grows, so a stale value is a safe bound; the tail in host memory is
+      // read again only when the head has caught up with the cached value)
       unsigned long long got = kNone;
+      int lane = 0;
       const long long t0 = clock64();
       unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(q.head);
       for (;;) {
+        const unsigned long long xt = ld_acquire_sys(&q.ctl->tail[1]);
+        unsigned long long xh = *reinterpret_cast<volatile unsigned long long*>(q.head + 1);
+        while (xh < xt) {
+          const unsigned long long seen = atomicCAS(q.head + 1, xh, xh + 1);
+          if (seen == xh) {
+            got = xh;
+            lane = 1;
+            break;
+          }
+          xh = seen;
+        }
+        if (got != kNone) break;
         if (h < tail_seen) {
           const unsigned long long seen = atomicCAS(q.head, h, h + 1);
           if (seen == h) {
@@ -305,7 +350,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
           h = seen;  // another CTA moved the head: retry from there
           continue;
         }
-        tail_seen = ld_acquire_sys(&q.ctl->tail);
+        tail_seen = ld_acquire_sys(&q.ctl->tail[0]);
         if (h < tail_seen) continue;
         if (ld_volatile_u32(&q.ctl->park)) break;
         if (clock64() - t0 > kIdleCycles) break;
@@ -315,7 +360,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       if (got != kNone) {
         // the slot is written before the tail moves; a withheld publication
         // leaves a stale sequence number: wait (bounded), then give up
-        WorkItem* slot = q.ring + (got % kRing);
+        WorkItem* slot = q.ring + (uint64_t)lane * kRing + (got % kRing);
         const long long t1 = clock64();
         while (ld_acquire_sys(&slot->seq) != got) {
           if (clock64() - t1 > kWaitCycles) {
@@ -330,6 +375,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         if (got != kSkip) s_item = *slot;
       }
       s_idx = got;
+      s_lane = lane;
       const long long now = clock64();
       cyc_wait += (unsigned long long)(now - t_mark);
       t_mark = now;
@@ -340,7 +386,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
     if (idx == kSkip) {
       if (tid == 0) {
         __threadfence_system();
-        atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed), 1ull);
+        atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed[s_lane]), 1ull);
       }
       __syncthreads();
       continue;
@@ -359,6 +405,10 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
     }
     switch (item.kind) {
       case K_BOX:  // the histogram's shared memory is free between forward items
+        // the first item also zeroes the cell counts (CELL items start only
+        // once every BOX item has finished)
+        if (item.begin == 0)
+          for (uint32_t k = tid; k < kOrderCells; k += blockDim.x) jd->cells[k] = 0u;
         box_range(jd->raw, item.begin, item.end, tid, blockDim.x, jd->cells + kOrderCells,
                   reinterpret_cast<uint32_t*>(sm.hist));
         break;
@@ -382,7 +432,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         // a forward wait that gave up is recorded in the job error word; the
         // stage barriers are then out of step with the unit counter: start
         // them afresh (every copy has landed or been waited for, bounded)
-        if (!fwd_item(*jd, item.begin, item.end, sm, it)) {
+        if (!fwd_item(*jd, sm, it)) {
           if (tid == 0) {
             for (int i = 0; i < 2 * kServeStages; ++i) mbar_inval(&sm.bars[i]);
             init_stage_barriers(sm.bars);
@@ -391,7 +441,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         }
         break;
       case K_REDUCE:
-        reduce_item(*jd, item.begin, item.end);
+        reduce_item(*jd, item.begin, item.end, reinterpret_cast<double*>(sm.hist));
         break;
       default:
         noise_item(*jd, item.begin, item.end);
@@ -401,7 +451,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
     if (tid == 0) {
       __threadfence_system();
       atomicAdd_system(&q.status[item.job].done[phase_of(item.kind)], 1u);
-      atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed), 1ull);
+      atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed[s_lane]), 1ull);
       const long long now = clock64();
       if (item.kind == K_FWD) cyc_fwd += (unsigned long long)(now - t_mark);
       else cyc_other += (unsigned long long)(now - t_mark);
@@ -455,7 +505,6 @@ struct Request {
   uint32_t withheld = 0;  // published items that will never complete (fault injection)
   std::vector<WorkItem> backlog;  // items of the current phase not yet published
   size_t backlog_pos = 0;
-  uint64_t first_item = 0, last_item = 0;
   bool release_on_done = false;
   Clock::time_point t_submit, t_done;
   Clock::time_point t_mark[2 + kPhases];  // tracing: admit, upload done, each phase done
@@ -491,9 +540,10 @@ struct Server {
   // kernel included) and cudaHostAlloc may synchronise too
   SceneScratch* h_scratch = nullptr;
   ServeArgs dev_args{};         // device addresses of the same memory
-  unsigned long long* d_head = nullptr;
-  uint64_t published = 0;
-  uint64_t window = 0;          // items outstanding on the device at most
+  unsigned long long* d_head = nullptr;  // [2]
+  uint64_t published[2] = {0, 0};       // per ring: main, express
+  uint64_t window[2] = {0, 0};          // items outstanding on the device at most, per ring
+  std::vector<std::pair<double, Request*>> fwd_order;  // publish_window's scratch
   bool kernel_running = false;
   cudaEvent_t kernel_done = nullptr;
   size_t smem = 0;
@@ -566,6 +616,9 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   a.bw = ((g.B + a.n_win - 1) / a.n_win + 3) & ~3u;
   a.n_blk = (a.n_pairs + a.ppb - 1) / a.ppb;
   a.units = (unsigned long long)((g.S + kTile - 1) / kTile) * a.n_win * a.n_blk;
+  a.next_chunk = &r->scratch->next_chunk;  // zero from the upload
+  a.chunk = std::min<unsigned long long>(
+      kFwdMaxChunk, std::max<unsigned long long>(1, a.units / ((uint64_t)sv.num_sms * kFwdChunksPerSm)));
   a.replicate = 0;
   if (g.bin_mode == NLOS_BIN_SPLAT) {
     const double s = g.sigma;
@@ -601,18 +654,22 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   j.nr_db = p.nr_db;
   j.seed = p.seed;
   j.tag = p.stream_tag;
-  (void)sv;
 }
 
-// Writes up to max_items backlog items of r into the ring and moves the tail
-// (release); returns how many it wrote.
+// The ring a phase's items go to: FORWARD to the main ring, the rest to the
+// express ring.
+int lane_of(int phase) { return phase == PH_FWD ? 0 : 1; }
+
+// Writes up to max_items backlog items of r into the ring of its phase and
+// moves that ring's tail (release); returns how many it wrote.
 size_t publish_some(Server& sv, Request* r, size_t max_items) {
   const size_t n = std::min(max_items, r->backlog.size() - r->backlog_pos);
   if (n == 0) return 0;
-  uint64_t idx = sv.published;
+  const int lane = lane_of(r->phase);
+  uint64_t idx = sv.published[lane];
   for (size_t k = 0; k < n; ++k) {
     const WorkItem& w = r->backlog[r->backlog_pos + k];
-    WorkItem* slot = sv.ring + (idx % kRing);
+    WorkItem* slot = sv.ring + (uint64_t)lane * kRing + (idx % kRing);
     slot->job = w.job;
     slot->kind = w.kind;
     slot->gen = w.gen;
@@ -630,10 +687,9 @@ size_t publish_some(Server& sv, Request* r, size_t max_items) {
     ++idx;
   }
   std::atomic_thread_fence(std::memory_order_seq_cst);
-  __atomic_store_n(&sv.ctl->tail, idx, __ATOMIC_RELEASE);
+  __atomic_store_n(&sv.ctl->tail[lane], idx, __ATOMIC_RELEASE);
   r->backlog_pos += n;
-  r->last_item = idx;
-  sv.published = idx;
+  sv.published[lane] = idx;
   if (r->backlog_pos == r->backlog.size()) {
     r->backlog.clear();
     r->backlog.shrink_to_fit();
@@ -642,20 +698,54 @@ size_t publish_some(Server& sv, Request* r, size_t max_items) {
   return n;
 }
 
-// Oldest request first: publishes backlog items of the running requests in
-// admission order while fewer than sv.window items are outstanding on the
-// device. Younger requests only fill what the older ones leave of the
-// window (their phase transitions, their last items), so a request's
-// latency is close to running it alone after the ones before it, while the
-// device stays busy. The window (a few items per SM) stays far below half
-// the ring, which the claim protocol requires.
+// Publishes backlog items of the running requests while fewer than the
+// ring's window of items are outstanding on the device. Express items go
+// oldest request first. FORWARD items: the oldest request with FORWARD work
+// may keep a quarter of the window outstanding, the rest goes shortest
+// remaining work first (the pairs of a request's unpublished FORWARD items).
+// A small request then does not wait behind the forward of a large one
+// submitted before it (which is what sets the median latency under first-in
+// first-out), while the oldest request keeps at least about a quarter of the
+// device, so a stream of small requests cannot starve a large one. (On a
+// replayed mixed trace, a half share gave a higher median, pure shortest-
+// remaining-first a longer tail, and aging by a fixed age both.) Each window (a few
+// items per SM) stays far below half its ring, which the claim protocol
+// requires.
 void publish_window(Server& sv) {
-  const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
-  uint64_t outstanding = sv.published - completed;
+  uint64_t outstanding[2];
+  for (int l = 0; l < 2; ++l)
+    outstanding[l] = sv.published[l] - __atomic_load_n(&sv.ctl->completed[l], __ATOMIC_ACQUIRE);
+  std::vector<std::pair<double, Request*>>& fwd = sv.fwd_order;
+  fwd.clear();
+  bool oldest = true;
   for (Request* r : sv.active) {
-    if (outstanding >= sv.window) break;
     if (r->state != R_RUNNING || r->backlog.empty()) continue;
-    outstanding += publish_some(sv, r, (size_t)(sv.window - outstanding));
+    const int l = lane_of(r->phase);
+    if (l == 0) {
+      if (oldest) {
+        oldest = false;
+        const uint64_t mine =
+            r->backlog_pos - __atomic_load_n(&sv.status[r->slot].done[PH_FWD], __ATOMIC_ACQUIRE);
+        const uint64_t share = sv.window[0] / 4;
+        if (mine < share && outstanding[0] < sv.window[0])
+          outstanding[0] += publish_some(
+              sv, r, (size_t)std::min(share - mine, sv.window[0] - outstanding[0]));
+        if (r->backlog.empty()) continue;
+      }
+      const double left = (double)(r->backlog.size() - r->backlog_pos) /
+                          (double)std::max<uint32_t>(1, r->items[PH_FWD]);
+      fwd.emplace_back(left * (double)r->g.S * (double)r->g.P, r);
+    } else if (outstanding[1] < sv.window[1]) {
+      outstanding[1] += publish_some(sv, r, (size_t)(sv.window[1] - outstanding[1]));
+    }
+  }
+  std::stable_sort(fwd.begin(), fwd.end(),
+                   [](const std::pair<double, Request*>& a, const std::pair<double, Request*>& b) {
+                     return a.first < b.first;
+                   });
+  for (auto& f : fwd) {
+    if (outstanding[0] >= sv.window[0]) break;
+    outstanding[0] += publish_some(sv, f.second, (size_t)(sv.window[0] - outstanding[0]));
   }
 }
 
@@ -679,15 +769,12 @@ void publish_phase(Server& sv, Request* r, int phase) {
     for (uint64_t b = 0; b < n; b += kZeroChunk)
       items.push_back({job, K_ZERO, gen, b, std::min<uint64_t>(n, b + kZeroChunk), 0});
   } else if (phase == PH_FWD) {
-    // point blocks per item: kFwdChunk, coarser for very large requests so a
-    // phase stays within kMaxPhaseItems (an item never spans two (tile, window))
+    // enough items for every chunk to be claimed: each claims kFwdClaims
+    // chunks unless the counter has passed the last one
     const FwdArgs& a = sv.jobs[job].fwd;
-    const uint64_t tws = a.units / a.n_blk;
-    uint64_t chunk = kFwdChunk;
-    while (chunk < a.n_blk && tws * ((a.n_blk + chunk - 1) / chunk) > kMaxPhaseItems) chunk *= 2;
-    for (uint64_t tw = 0; tw < tws; ++tw)
-      for (uint64_t b = 0; b < a.n_blk; b += chunk)
-        items.push_back({job, K_FWD, gen, tw * a.n_blk + b, tw * a.n_blk + std::min<uint64_t>(a.n_blk, b + chunk), 0});
+    const uint64_t chunks = (a.units + a.chunk - 1) / a.chunk;
+    const uint64_t n_items = (chunks + kFwdClaims - 1) / kFwdClaims;
+    for (uint64_t i = 0; i < n_items; ++i) items.push_back({job, K_FWD, gen, 0, 0, 0});
   } else if (phase == PH_REDUCE) {
     for (uint64_t b = 0; b < g.S; b += kReduceChunk)
       items.push_back({job, K_REDUCE, gen, b, std::min<uint64_t>(g.S, b + kReduceChunk), 0});
@@ -893,9 +980,11 @@ bool step(Server& sv) {
   }
   publish_window(sv);
   // kernel lifecycle: run while items are outstanding, park when idle
-  const uint64_t completed = __atomic_load_n(&sv.ctl->completed, __ATOMIC_ACQUIRE);
+  bool outstanding = false;
+  for (int l = 0; l < 2; ++l)
+    outstanding |= sv.published[l] > __atomic_load_n(&sv.ctl->completed[l], __ATOMIC_ACQUIRE);
   if (sv.kernel_running && cudaEventQuery(sv.kernel_done) == cudaSuccess) sv.kernel_running = false;
-  if (sv.published > completed && !sv.kernel_running) {
+  if (outstanding && !sv.kernel_running) {
     __atomic_store_n(&sv.ctl->park, 0u, __ATOMIC_RELEASE);
     ServeArgs q = sv.dev_args;
     serve_kernel<<<sv.num_sms, kServeThreads, sv.smem, sv.kstream>>>(q);
@@ -908,8 +997,9 @@ bool step(Server& sv) {
 }
 
 // Uploader thread: scan table, tile bounds, points, a zeroed scratch and the
-// ordering's initial counts and box of each admitted request on the copy
-// stream, then the request's event.
+// ordering's initial box of each admitted request on the copy stream, then
+// the request's event. Only copies go to that stream: a memset or a kernel
+// there would wait for an SM, and the serving kernel may hold all of them.
 void upload_loop(Server* sv) {
   cudaSetDevice(sv->device);
   for (;;) {
@@ -937,8 +1027,6 @@ void upload_loop(Server* sv) {
       e = cudaMemcpyAsync(r->raw, r->pts.data(), sizeof(float) * 8 * r->g.P,
                           cudaMemcpyHostToDevice, sv->cstream);
     if (e == cudaSuccess)
-      e = cudaMemsetAsync(r->cells, 0, sizeof(uint32_t) * kOrderCells, sv->cstream);
-    if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->cells + kOrderCells, box0, sizeof(box0), cudaMemcpyHostToDevice,
                           sv->cstream);
     if (e == cudaSuccess)
@@ -952,12 +1040,17 @@ void upload_loop(Server* sv) {
 
 void run(Server* sv) {
   cudaSetDevice(sv->device);
+#ifdef __linux__
+  // the default timer slack (50 us) would stretch the short sleeps between
+  // scheduler passes, and with them every phase transition of a request
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
   std::unique_lock<std::mutex> lk(sv->mu);
   while (!sv->stop.load()) {
     const bool busy = step(*sv);
     if (busy) {
       lk.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(10));
+      std::this_thread::sleep_for(std::chrono::microseconds(5));
       lk.lock();
     } else {
       sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
@@ -1001,23 +1094,23 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
   if (e != cudaSuccess) return fail(e, "cudaGetDevice");
   const unsigned flags = cudaHostAllocMapped | cudaHostAllocPortable;
   if ((e = cudaHostAlloc(&sv.ctl, sizeof(Control), flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
-  if ((e = cudaHostAlloc(&sv.ring, sizeof(WorkItem) * kRing, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
+  if ((e = cudaHostAlloc(&sv.ring, sizeof(WorkItem) * 2 * kRing, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
   if ((e = cudaHostAlloc(&sv.jobs, sizeof(JobDesc) * kMaxJobs, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
   if ((e = cudaHostAlloc(&sv.status, sizeof(JobStatus) * kMaxJobs, flags)) != cudaSuccess) return fail(e, "cudaHostAlloc");
   if ((e = cudaHostAlloc(&sv.h_scratch, sizeof(SceneScratch) * kMaxJobs, cudaHostAllocPortable)) != cudaSuccess)
     return fail(e, "cudaHostAlloc");
   std::memset(sv.ctl, 0, sizeof(Control));
-  std::memset(sv.ring, 0xff, sizeof(WorkItem) * kRing);  // seq = ~0: unpublished
+  std::memset(sv.ring, 0xff, sizeof(WorkItem) * 2 * kRing);  // seq = ~0: unpublished
   std::memset(sv.jobs, 0, sizeof(JobDesc) * kMaxJobs);
   std::memset(sv.status, 0, sizeof(JobStatus) * kMaxJobs);
-  if ((e = cudaMalloc(&sv.d_head, sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc");
+  if ((e = cudaMalloc(&sv.d_head, 2 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc");
   if ((e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.ctl), sv.ctl, 0)) != cudaSuccess ||
       (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.ring), sv.ring, 0)) != cudaSuccess ||
       (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.jobs), sv.jobs, 0)) != cudaSuccess ||
       (e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sv.dev_args.status), sv.status, 0)) != cudaSuccess)
     return fail(e, "cudaHostGetDevicePointer");
   sv.dev_args.head = sv.d_head;
-  if ((e = cudaMemset(sv.d_head, 0, sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMemset");
+  if ((e = cudaMemset(sv.d_head, 0, 2 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMemset");
   if ((e = cudaStreamCreateWithFlags(&sv.kstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
   if ((e = cudaStreamCreateWithFlags(&sv.cstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e, "cudaStreamCreate");
   if ((e = cudaEventCreateWithFlags(&sv.kernel_done, cudaEventDisableTiming)) != cudaSuccess) return fail(e, "cudaEventCreate");
@@ -1027,11 +1120,12 @@ nlos_status nlos_server_create(uint64_t hbm_budget_bytes, nlos_server** out) {
     return fail(e, "cudaFuncSetAttribute");
   cudaDeviceSynchronize();
   for (int i = kMaxJobs - 1; i >= 0; --i) sv.free_slots.push_back(i);
-  sv.window = std::min<uint64_t>(kWindowPerSm * (uint64_t)sv.num_sms, kRing / 2);
+  sv.window[0] = std::min<uint64_t>(kWindowPerSm * (uint64_t)sv.num_sms, kRing / 4);
+  sv.window[1] = std::min<uint64_t>(kXWindowPerSm * (uint64_t)sv.num_sms, kRing / 4);
   if (const char* tp = std::getenv("NLOS_SERVE_TRACE")) sv.trace = std::fopen(tp, "a");
   sv.th = std::thread(run, &sv);
-  // several uploaders: ordering a request's points on the host takes ~10 ns
-  // per point, and requests are independent
+  // several uploaders: a copy from pageable memory returns once the data is
+  // staged, and requests are independent
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
   for (unsigned i = 0; i < std::min(4u, std::max(1u, hw / 4)); ++i)
     sv.uploaders.emplace_back(upload_loop, &sv);
