@@ -75,6 +75,39 @@ def geom(params: dict) -> Geom:
     )
 
 
+class Occluder(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("a", ctypes.c_double * 3), ("b", ctypes.c_double * 3)]
+
+
+# Visibility threshold: a segment is blocked when its chord inside an occluder
+# exceeds this fraction of its length (a reading of this build; the paper's
+# model has no visibility term).
+OCC_ETA = 4e-3
+
+
+def occluders(recs) -> ctypes.Array:
+    """Occluder records [n, 8] (kind, a0, a1, a2, b0, b1, b2, unused; kind 0 =
+    sphere with centre a and radius b0, kind 1 = box with corners a < b), as
+    float32 values promoted exactly to float64."""
+    r = np.asarray(recs, dtype=np.float32).reshape(-1, 8).astype(np.float64)
+    arr = (Occluder * max(1, len(r)))()
+    for i, o in enumerate(r):
+        arr[i].kind = int(o[0])
+        for k in range(3):
+            arr[i].a[k] = o[1 + k]
+            arr[i].b[k] = o[4 + k]
+    return arr
+
+
+def chord(rec, x, y) -> float:
+    """Fraction of segment x -> y strictly inside the occluder ``rec``."""
+    lib = _load()
+    o = occluders([rec])
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    ya = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib.orc_chord(o, _ptr(xa), _ptr(ya)))
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -94,6 +127,11 @@ def _load():
             lib.orc_pair_table.argtypes = [_GP, _I64, _P, _P, _I64, _P, _P, ctypes.c_int]
             lib.orc_forward_binned.argtypes = [_GP, _I64, _P, _I64, _I64, _P, _D, _P, _P, _P,
                                                ctypes.c_int]
+            lib.orc_chord.argtypes = [ctypes.POINTER(Occluder), _P, _P]
+            lib.orc_chord.restype = _D
+            lib.orc_forward_binned_vis.argtypes = [_GP, _I64, _P, _I64, _I64,
+                                                   ctypes.POINTER(Occluder), ctypes.c_int32, _D,
+                                                   _D, _P, _D, _P, _P, _P, _P, _P, ctypes.c_int]
             lib.orc_jitter_taps.argtypes = [_D, _D, _P, ctypes.c_int]
             lib.orc_jitter.argtypes = [_P, _I64, ctypes.c_int32, _P, ctypes.c_int32, _P]
             lib.orc_jitter_padded.argtypes = [_P, _I64, ctypes.c_int32, _P, ctypes.c_int32,
@@ -165,11 +203,19 @@ def pair_table(params, pts, scan_ids, threads: int = 0):
 
 
 def forward_binned(params, pts, s_begin: int = 0, s_count: int | None = None,
-                   eps: float = 0.0, threads: int = 0):
+                   eps: float = 0.0, threads: int = 0, occ=None, eta: float = OCC_ETA,
+                   occ_delta: float = 0.0):
     """Binned transient tau[s, b] (float64) for scan points s_begin..s_begin+s_count.
 
     With eps > 0 also returns the per-bin mass of pairs within eps of a bin edge
-    (``flip_mass``), its window-edge part (``edge_mass``) and their count."""
+    (``flip_mass``), its window-edge part (``edge_mass``) and their count.
+    With occluder records ``occ`` ([n, 8], see ``occluders``), pairs whose point
+    is hidden from one of its spots are left out; ``occ_mass`` / ``n_occ_border``
+    are the weight and count of pairs whose chord lies within ``occ_delta`` of
+    ``eta``."""
+    if occ is not None and len(np.asarray(occ).reshape(-1, 8)) > 0:
+        return _forward_binned_vis(params, pts, s_begin, s_count, eps, threads, occ, eta,
+                                   occ_delta)
     lib = _load()
     g = geom(params)
     P = _pts64(pts)
@@ -187,6 +233,33 @@ def forward_binned(params, pts, s_begin: int = 0, s_count: int | None = None,
                            float(eps), _ptr(flip) if flip is not None else None,
                            _ptr(edge) if edge is not None else None, _ptr(nb), threads)
     return dict(tau=tau, flip_mass=flip, edge_mass=edge, n_boundary=int(nb[0]))
+
+
+def _forward_binned_vis(params, pts, s_begin, s_count, eps, threads, occ, eta, occ_delta):
+    lib = _load()
+    g = geom(params)
+    P = _pts64(pts)
+    S = num_scan(params)
+    if s_count is None:
+        s_count = S - s_begin
+    if not (0 <= s_begin and s_begin + s_count <= S):
+        raise ValueError("scan range out of bounds")
+    B = int(params["num_bins"])
+    o = occluders(occ)
+    n_occ = len(np.asarray(occ).reshape(-1, 8))
+    tau = np.zeros((s_count, B))
+    flip = np.zeros((s_count, B)) if eps > 0 else None
+    edge = np.zeros(s_count) if eps > 0 else None
+    om = np.zeros((s_count, B))
+    nb = np.zeros(1, dtype=np.int64)
+    no = np.zeros(1, dtype=np.int64)
+    lib.orc_forward_binned_vis(ctypes.byref(g), P.shape[0], _ptr(P), s_begin, s_count, o, n_occ,
+                               float(eta), float(occ_delta), _ptr(tau), float(eps),
+                               _ptr(flip) if flip is not None else None,
+                               _ptr(edge) if edge is not None else None, _ptr(nb), _ptr(om),
+                               _ptr(no), threads)
+    return dict(tau=tau, flip_mass=flip, edge_mass=edge, n_boundary=int(nb[0]), occ_mass=om,
+                n_occ_border=int(no[0]))
 
 
 def sigma_bins(fwhm_s: float, bin_width_s: float) -> float:

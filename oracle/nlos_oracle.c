@@ -20,7 +20,8 @@
  *    convention of Eq. 1).
  *  - Bin b holds u in [b, b+1); pairs with u < 0 or u >= B are dropped.
  *  - Object-side cosines are clamped at zero (back-facing patches give no
- *    light); no other factor is clamped; no visibility test (Eq. 1 has none).
+ *    light); no other factor is clamped; no visibility test (Eq. 1 has none)
+ *    unless the caller attaches occluders (an extension, see below).
  *  - Jitter taps are normalised to sum 1 and the trace is zero-padded.
  *  - Noise follows Algorithm 1: blur first, then Poisson.
  */
@@ -154,6 +155,141 @@ int orc_forward_binned(const orc_geom* g, int64_t num_points, const double* pts,
     }
   }
   if (n_boundary) *n_boundary = nb_total;
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Visibility (an extension: the paper's model, Eq. 1, has no visibility term,
+ * and its depth maps keep only the first surface seen from the wall).
+ * Occluders are convex solids: spheres (centre a, radius b[0]) and
+ * axis-aligned boxes (corners a < b). The chord of a segment x -> y through
+ * an occluder is the length, in units of the segment, of the set
+ *   { t in [0, 1] : x + t (y - x) lies strictly inside the occluder },
+ * an interval because the solid is convex. A pair (s, p) is seen when the
+ * chord of the segment from each of its spots (laser l_s and detector d_s;
+ * one segment when they coincide) to the point is at most eta in every
+ * occluder. The tolerance eta (a small fraction of the segment) keeps a
+ * point on an occluder's own surface, whose segments leave the solid at
+ * once, visible whatever the rounding of its coordinates.
+ * ------------------------------------------------------------------------- */
+double orc_chord(const orc_occluder* o, const double x[3], const double y[3]) {
+  const double d[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+  double t0 = 0.0, t1 = 1.0;
+  if (o->kind == 0) {
+    /* |x + t d - c|^2 < r^2:  A t^2 + 2 B t + C < 0 */
+    const double f[3] = {x[0] - o->a[0], x[1] - o->a[1], x[2] - o->a[2]};
+    const double A = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double B = f[0] * d[0] + f[1] * d[1] + f[2] * d[2];
+    const double C = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] - o->b[0] * o->b[0];
+    if (A == 0.0) return 0.0;
+    const double disc = B * B - A * C;
+    if (disc <= 0.0) return 0.0;
+    const double sq = sqrt(disc);
+    const double lo = (-B - sq) / A, hi = (-B + sq) / A;
+    if (lo > t0) t0 = lo;
+    if (hi < t1) t1 = hi;
+  } else {
+    /* slabs: a_k < x_k + t d_k < b_k for k = 0, 1, 2 */
+    for (int k = 0; k < 3; ++k) {
+      if (d[k] == 0.0) {
+        if (!(o->a[k] < x[k] && x[k] < o->b[k])) return 0.0;
+        continue;
+      }
+      double ta = (o->a[k] - x[k]) / d[k], tb = (o->b[k] - x[k]) / d[k];
+      if (ta > tb) {
+        const double tmp = ta;
+        ta = tb;
+        tb = tmp;
+      }
+      if (ta > t0) t0 = ta;
+      if (tb < t1) t1 = tb;
+    }
+  }
+  return t1 > t0 ? t1 - t0 : 0.0;
+}
+
+/* Visibility of point pt from spot z (a point of the wall): 1 if no chord
+ * exceeds eta; *border is set when some chord lies within delta of eta. */
+static int seen_from(const double z[3], const double* pt, const orc_occluder* occ, int32_t n_occ,
+                     double eta, double delta, int* border) {
+  int seen = 1;
+  for (int32_t k = 0; k < n_occ; ++k) {
+    const double c = orc_chord(occ + k, z, pt);
+    if (c > eta) seen = 0;
+    if (fabs(c - eta) < delta) *border = 1;
+  }
+  return seen;
+}
+
+/* ---------------------------------------------------------------------------
+ * Binned forward with occluders: as orc_forward_binned, with each pair's
+ * weight kept only when the point is seen from both of its spots. occ_mass
+ * (optional) gets, per bin, the weight of in-window pairs whose visibility
+ * lies within delta of the threshold (such a pair may legitimately come out
+ * either way in a lower-precision evaluation); n_occ_border counts them.
+ * ------------------------------------------------------------------------- */
+int orc_forward_binned_vis(const orc_geom* g, int64_t num_points, const double* pts,
+                           int64_t s_begin, int64_t s_count, const orc_occluder* occ,
+                           int32_t n_occ, double eta, double delta, double* tau, double eps,
+                           double* flip_mass, double* edge_mass, int64_t* n_boundary,
+                           double* occ_mass, int64_t* n_occ_border, int num_threads) {
+  const int32_t B = g->num_bins;
+  const double L0 = orc_window_start(g);
+  int64_t nb_total = 0, no_total = 0;
+  memset(tau, 0, sizeof(double) * (size_t)s_count * (size_t)B);
+  if (flip_mass) memset(flip_mass, 0, sizeof(double) * (size_t)s_count * (size_t)B);
+  if (edge_mass) memset(edge_mass, 0, sizeof(double) * (size_t)s_count);
+  if (occ_mass) memset(occ_mass, 0, sizeof(double) * (size_t)s_count * (size_t)B);
+#ifdef _OPENMP
+  if (num_threads <= 0) num_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(num_threads) reduction(+ : nb_total, no_total)
+#endif
+  for (int64_t i = 0; i < s_count; ++i) {
+    double l[3], d[3], legs;
+    orc_scan_geometry(g, s_begin + i, l, d, &legs);
+    const int same = l[0] == d[0] && l[1] == d[1] && l[2] == d[2];
+    double* row = tau + i * B;
+    for (int64_t p = 0; p < num_points; ++p) {
+      const double* pt = pts + 8 * p;
+      double u, w;
+      pair_at(g, l, d, legs, L0, pt, &u, &w);
+      int border = 0;
+      int seen = 1;
+      if (n_occ > 0) {
+        seen = seen_from(d, pt, occ, n_occ, eta, delta, &border);
+        if (!same) seen = seen_from(l, pt, occ, n_occ, eta, delta, &border) && seen;
+      }
+      const int in = u >= 0.0 && u < (double)B;
+      if (in && seen) row[(int64_t)floor(u)] += w;
+      if (border && in && w != 0.0) {
+        no_total += 1;
+        if (occ_mass) {
+          const int64_t b = (int64_t)floor(u);
+          occ_mass[i * B + b] += fabs(w);
+          /* near a bin edge the pair may also land in the neighbouring bin */
+          const double m = floor(u + 0.5);
+          if (eps > 0.0 && fabs(u - m) < eps) {
+            const int64_t nbr = (int64_t)m == b ? b - 1 : b + 1;
+            if (nbr >= 0 && nbr < B) occ_mass[i * B + nbr] += fabs(w);
+          }
+        }
+      }
+      if (eps > 0.0 && seen) {
+        double m = floor(u + 0.5);
+        if (fabs(u - m) < eps && m >= 0.0 && m <= (double)B) {
+          int64_t mi = (int64_t)m;
+          nb_total += 1;
+          if (flip_mass) {
+            if (mi >= 1) flip_mass[i * B + mi - 1] += w;
+            if (mi < B) flip_mass[i * B + mi] += w;
+          }
+          if (edge_mass && (mi == 0 || mi == B)) edge_mass[i] += w;
+        }
+      }
+    }
+  }
+  if (n_boundary) *n_boundary = nb_total;
+  if (n_occ_border) *n_occ_border = no_total;
   return 0;
 }
 

@@ -60,6 +60,27 @@ int orc_forward_binned(const orc_geom* g, int64_t num_points, const double* pts,
                        double eps, double* flip_mass, double* edge_mass,
                        int64_t* n_boundary, int num_threads);
 
+/* Occluders (an extension; the paper's model has no visibility term):
+ * kind 0 = sphere (a = centre, b[0] = radius), kind 1 = axis-aligned box
+ * (corners a < b). */
+typedef struct {
+  int32_t kind;
+  double a[3], b[3];
+} orc_occluder;
+
+/* Length, in units of the segment, of the part of segment x -> y strictly
+ * inside the occluder. */
+double orc_chord(const orc_occluder* o, const double x[3], const double y[3]);
+
+/* Binned forward with the pairs whose point is hidden from one of its spots
+ * (a chord above eta) left out; occ_mass / n_occ_border: pairs whose chord
+ * lies within delta of eta. */
+int orc_forward_binned_vis(const orc_geom* g, int64_t num_points, const double* pts,
+                           int64_t s_begin, int64_t s_count, const orc_occluder* occ,
+                           int32_t n_occ, double eta, double delta, double* tau, double eps,
+                           double* flip_mass, double* edge_mass, int64_t* n_boundary,
+                           double* occ_mass, int64_t* n_occ_border, int num_threads);
+
 /* Gaussian jitter (Eq. 16/17). */
 int orc_jitter_taps(double fwhm_s, double bin_width_s, double* taps, int max_taps);
 void orc_jitter(const double* tau, int64_t num_traces, int32_t num_bins,
