@@ -337,12 +337,55 @@ def run_ours(args):
         line["serving"] = serving_bench(args.serving_requests, args.serving_rate)
     if rank == 0 and ws == 1 and args.lct_steps > 0:
         line["lct"] = lct_bench(args.lct_steps)
+    if rank == 0 and ws == 1 and args.occlusion_steps > 0:
+        line["occlusion"] = occlusion_bench(args.occlusion_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     scene.destroy()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def occlusion_bench(steps: int):
+    """The union workload's forward with its own spheres and boxes as
+    occluders (the visibility extension: one segment test per binned pair and
+    occluder) against the same forward without them; L2 flushed between
+    launches. Effective pairs/s = S * P / time."""
+    import torch
+    import scenes
+    from paper_2506_03747_gb300 import nlos
+    params, _ = scenes.workload_union64()
+    rng = np.random.default_rng(scenes.SEED_BASE + 2)
+    pts, prims = scenes.primitive_union_points(rng, 262144)
+    occ = scenes.occluder_records(prims)
+    sc = nlos.scene_create(nlos.params(params), torch.from_numpy(pts).cuda())
+    S, B = sc.num_scan, sc.num_bins
+    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, o in (("without", None), ("with", occ)):
+        nlos.scene_set_occluders(sc, o)
+        for _ in range(3):
+            nlos.forward(sc, tau)
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            nlos.forward(sc, tau)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = float(np.median(ts))
+    sc.destroy()
+    pairs = S * len(pts)
+    return {"workload": f"union64 ({S} scan points x {len(pts)} points, 512 bins) with its "
+                        f"{len(occ)} primitives as occluders",
+            "occluders": len(occ), "forward_ms_without": out["without"],
+            "forward_ms_with": out["with"],
+            "effective_pairs_per_s_with": pairs / (out["with"] * 1e-3),
+            "slowdown": out["with"] / out["without"]}
 
 
 def lct_bench(steps: int):
@@ -599,6 +642,8 @@ def main():
                     help="steps of the differentiable-path measurement (0: skip)")
     ap.add_argument("--lct-steps", type=int, default=3,
                     help="timed passes of the FFT forward model comparison (0: skip)")
+    ap.add_argument("--occlusion-steps", type=int, default=5,
+                    help="timed forwards of the occlusion leg (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests in the serving replay (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=200.0,

@@ -166,6 +166,28 @@ nlos_status nlos_scene_create(const nlos_params* params, const float* points_aos
 nlos_status nlos_scene_set_points(nlos_scene* scene, const float* points_aos8, uint64_t num_points,
                                   int points_on_device, void* cuda_stream);
 
+/* Occluders: an extension; the paper's model (Eq. 1) has no visibility term,
+ * its depth maps keeping only the first surface seen from the wall. A scene
+ * may carry up to NLOS_MAX_OCCLUDERS convex solids, each a record of 8
+ * floats {kind, a0, a1, a2, b0, b1, b2, unused}: kind 0 = sphere with centre
+ * a and radius b0 > 0, kind 1 = axis-aligned box with corners a < b (per
+ * axis). The binned forward then leaves out a pair (s, p) when the segment
+ * from its detector spot d_s, or from its laser spot l_s, to the point runs
+ * strictly inside some occluder for more than NLOS_OCC_ETA of its length;
+ * the tolerance keeps a point on an occluder's own surface visible under
+ * FP32 rounding. Non-confocal scans test the laser leg once per point when
+ * the points are packed (FP64); the detector leg is tested per pair (FP32).
+ * occluders: host memory, copied; count 0 removes them. The points are
+ * re-packed on cuda_stream (asynchronous). NLOS_EINVAL: count above
+ * NLOS_MAX_OCCLUDERS, an unknown kind, a non-finite value, a radius <= 0 or
+ * a box with a >= b on some axis. While a scene has occluders, nlos_forward
+ * and nlos_simulate need bin_mode = NLOS_BIN_NEAREST and boundary_eps = 0
+ * (NLOS_EINVAL otherwise), and nlos_pair_table ignores them. */
+#define NLOS_MAX_OCCLUDERS 16
+#define NLOS_OCC_ETA 4e-3f
+nlos_status nlos_scene_set_occluders(nlos_scene* scene, const float* occluders, uint32_t count,
+                                     void* cuda_stream);
+
 /* Waits for cuda_stream and reports invalid points or a device wait that gave
  * up since the scene was created (NLOS_EINVAL / NLOS_ETIMEOUT). */
 nlos_status nlos_scene_check(nlos_scene* scene, void* cuda_stream);

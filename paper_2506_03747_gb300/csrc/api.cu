@@ -110,6 +110,37 @@ nlos_status nlos_scene_set_points(nlos_scene* scene, const float* points_aos8, u
   return scene_set_points(scene, points_aos8, num_points, points_on_device, as_stream(cuda_stream));
 }
 
+nlos_status nlos_scene_set_occluders(nlos_scene* scene, const float* occluders, uint32_t count,
+                                     void* cuda_stream) {
+  clear_error();
+  if (!scene) return set_error(NLOS_EINVAL, "scene is NULL");
+  if (count > (uint32_t)kMaxOcc) return set_error(NLOS_EINVAL, "more than NLOS_MAX_OCCLUDERS occluders");
+  if (count && !occluders) return set_error(NLOS_EINVAL, "occluders is NULL");
+  OccSet o{};
+  o.n = (int)count;
+  o.eta = NLOS_OCC_ETA;
+  for (uint32_t k = 0; k < count; ++k) {
+    const float* r = occluders + 8 * k;
+    for (int c = 0; c < 7; ++c)
+      if (!std::isfinite(r[c])) return set_error(NLOS_EINVAL, "non-finite occluder value");
+    if (r[0] == 0.f) {
+      if (!(r[4] > 0.f)) return set_error(NLOS_EINVAL, "sphere occluder with radius <= 0");
+    } else if (r[0] == 1.f) {
+      if (!(r[1] < r[4] && r[2] < r[5] && r[3] < r[6]))
+        return set_error(NLOS_EINVAL, "box occluder needs a < b on every axis");
+    } else {
+      return set_error(NLOS_EINVAL, "unknown occluder kind (0 sphere, 1 box)");
+    }
+    o.occ[2 * k] = make_float4(r[1], r[2], r[3], r[0]);
+    o.occ[2 * k + 1] = make_float4(r[4], r[5], r[6], 0.f);
+  }
+  SceneImpl& s = scene->impl;
+  s.occ = o;
+  if (s.g.P == 0) return NLOS_OK;
+  NLOS_CUDA_TRY(launch_order_pack(s, as_stream(cuda_stream)));
+  return NLOS_OK;
+}
+
 nlos_status nlos_scene_check(nlos_scene* scene, void* cuda_stream) {
   clear_error();
   if (!scene) return set_error(NLOS_EINVAL, "scene is NULL");
@@ -132,6 +163,8 @@ nlos_status nlos_forward(nlos_scene* scene, float* tau_dev, void* cuda_stream) {
   SceneImpl& s = scene->impl;
   if (!tau_dev || !aligned16(tau_dev))
     return set_error(NLOS_EINVAL, "tau_dev must be a 16-byte aligned device pointer");
+  if (s.occ.n > 0 && (s.g.bin_mode != NLOS_BIN_NEAREST || s.params.boundary_eps > 0.f))
+    return set_error(NLOS_EINVAL, "occluders need bin_mode = NLOS_BIN_NEAREST and boundary_eps = 0");
   cudaStream_t st = as_stream(cuda_stream);
   NLOS_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(s.scratch) + kScratchResetOffset, 0,
                                 sizeof(SceneScratch) - kScratchResetOffset, st));

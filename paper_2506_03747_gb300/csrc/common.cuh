@@ -143,6 +143,17 @@ cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scrat
 cudaError_t launch_philox(const uint32_t* ctr, uint64_t n, uint32_t k0, uint32_t k1,
                           uint32_t* out, cudaStream_t st);
 
+// Occluders of a scene (visibility extension): occ[2k] = (a.xyz, kind),
+// occ[2k + 1] = (b.xyz, 0); kind 0 = sphere (centre a, radius b.x), 1 = box
+// (corners a < b). Passed by value to the kernels that need it.
+constexpr int kMaxOcc = NLOS_MAX_OCCLUDERS;
+struct __align__(16) OccSet {
+  int n;       // occluders in use (0: no visibility test)
+  float eta;   // chord threshold, fraction of the segment
+  float pad[2];
+  float4 occ[2 * kMaxOcc];
+};
+
 // Scene internals shared by the host code of the library.
 struct SceneImpl {
   nlos_params params;
@@ -156,6 +167,7 @@ struct SceneImpl {
   uint32_t* cells = nullptr;       // [kOrderCells + 8] counts/cursors + box (ordering scratch)
   BlockBound* bounds = nullptr;    // [ceil(P / 2 / kSubPairs)]
   TileBound* tiles = nullptr;      // [ceil(S / kTile)]
+  OccSet occ{};                    // occluders (host copy; n = 0: none)
   cudaStream_t stream = nullptr;   // creation stream
   int device = 0;
   int num_sms = 0;

@@ -28,7 +28,8 @@ namespace nlos {
 // job's work units from a counter in the scene scratch.
 template <int SCAN, int COS, int MODE>
 __global__ void __launch_bounds__(1024, 1)
-    fwd_kernel(const __grid_constant__ FwdArgs a, const __grid_constant__ MomTab mt) {
+    fwd_kernel(const __grid_constant__ FwdArgs a, const __grid_constant__ MomTab mt,
+               const __grid_constant__ OccSet occ) {
   extern __shared__ __align__(128) unsigned char smem[];
   FwdSmem sm;
   const size_t hist_bytes = (MODE == MODE_SPLAT_MOM) ? (size_t)kMoments * kMomRows * kTile * 4
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(1024, 1)
   FwdCount cnt;
   uint32_t it = 0;
   (void)fwd_run_ws<SCAN, COS, MODE>(a, 0, 0, sm, (int)a.stages, cnt, &mt, it, a.next_chunk,
-                                    a.chunk, a.units);
+                                    a.chunk, a.units, 0, &occ);
   if (MODE == MODE_NEAREST_COUNT && cnt.boundary) atomicAdd(a.boundary, cnt.boundary);
   // the count is warp-uniform: one lane adds it, 64 pairs per warp iteration
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
@@ -99,13 +100,14 @@ __global__ void pair_table_kernel(const PairTableArgs t, const ScanPoint* scan, 
 // ---------------------------------------------------------------------------
 namespace {
 
-using FwdFn = void (*)(FwdArgs, MomTab);
+using FwdFn = void (*)(FwdArgs, MomTab, OccSet);
 
 template <int SCAN, int COS>
 FwdFn pick_mode(int mode) {
   switch (mode) {
     case MODE_NEAREST: return fwd_kernel<SCAN, COS, MODE_NEAREST>;
     case MODE_NEAREST_COUNT: return fwd_kernel<SCAN, COS, MODE_NEAREST_COUNT>;
+    case MODE_NEAREST_OCC: return fwd_kernel<SCAN, COS, MODE_NEAREST_OCC>;
     case MODE_SPLAT_MOM: return fwd_kernel<SCAN, COS, MODE_SPLAT_MOM>;
     default: return fwd_kernel<SCAN, COS, MODE_SPLAT>;
   }
@@ -175,7 +177,9 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   const bool moments = splat && use_moments(g.sigma);
   const int mode = moments ? MODE_SPLAT_MOM
                    : splat ? MODE_SPLAT
-                           : (sc.params.boundary_eps > 0.f ? MODE_NEAREST_COUNT : MODE_NEAREST);
+                   : sc.params.boundary_eps > 0.f ? MODE_NEAREST_COUNT
+                   : sc.occ.n > 0 ? MODE_NEAREST_OCC
+                                  : MODE_NEAREST;
   if (moments) moment_table(g.sigma, mt);
   a.eps = sc.params.boundary_eps;
   if (splat) {
@@ -249,7 +253,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   // about 8 chunks per CTA on average: fine enough to even out units whose
   // cost differs (the early out), coarse enough to keep flushes rare
   a.chunk = std::max<unsigned long long>(1, a.units / (grid * NLOS_FWD_CHUNKS_PER_CTA));
-  fn<<<(unsigned)grid, threads, smem, st>>>(a, mt);
+  fn<<<(unsigned)grid, threads, smem, st>>>(a, mt, sc.occ);
   return cudaGetLastError();
 }
 

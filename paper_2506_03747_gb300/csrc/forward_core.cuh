@@ -57,7 +57,8 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
 #endif
 
-enum { MODE_NEAREST = 0, MODE_NEAREST_COUNT = 1, MODE_SPLAT = 2, MODE_SPLAT_MOM = 3 };
+enum { MODE_NEAREST = 0, MODE_NEAREST_COUNT = 1, MODE_SPLAT = 2, MODE_SPLAT_MOM = 3,
+       MODE_NEAREST_OCC = 4 /* NEAREST with the occluder visibility test */ };
 
 // Moment form of the splat (standalone forward, sigma >= 2.5 bins): per bin m
 // and scan point, M_n[m] = sum of w c^n over the pairs with floor(u) = m,
@@ -488,11 +489,60 @@ __device__ __forceinline__ void red_moments(uint32_t addr, float w, float c, uin
   red_moment<5>(addr, wk, ok);
 }
 
+// Visibility of the point S + d from the spot S = (sx, sy, 0) (the detector
+// leg of a pair; A = |d|^2 > 0, d.z > 0): false when the segment runs
+// strictly inside an occluder for more than o.eta of its length. Spheres: the
+// chord in units of A (no division), from |S + t d - c|^2 < r^2; boxes: the
+// slab intervals of t, with reciprocal estimates. The threshold is far above
+// the FP32 rounding of the chord except for near-tangent segments, which the
+// parity tests treat like pairs near a bin edge.
+__device__ __forceinline__ bool occ_seen(const OccSet& o, float sx, float sy, float dx, float dy,
+                                         float dz, float A) {
+  for (int k = 0; k < o.n; ++k) {
+    const float4 p = o.occ[2 * k], q = o.occ[2 * k + 1];
+    if (p.w == 0.f) {
+      const float fx = sx - p.x, fy = sy - p.y;
+      const float B = fmaf(fx, dx, fmaf(fy, dy, -p.z * dz));
+      const float C = fmaf(fx, fx, fmaf(fy, fy, fmaf(p.z, p.z, -q.x * q.x)));
+      const float disc = fmaf(B, B, -A * C);
+      if (disc > 0.f) {
+        const float sq = sqrt_approx(disc);
+        const float t0 = fmaxf(-B - sq, 0.f), t1 = fminf(-B + sq, A);
+        if (t1 - t0 > o.eta * A) return false;
+      }
+    } else {
+      float t0 = 0.f, t1 = 1.f;
+      bool miss = false;
+      if (dx != 0.f) {
+        const float r = rcp_approx(dx);
+        const float ta = (p.x - sx) * r, tb = (q.x - sx) * r;
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+      } else {
+        miss = !(p.x < sx && sx < q.x);
+      }
+      if (dy != 0.f) {
+        const float r = rcp_approx(dy);
+        const float ta = (p.y - sy) * r, tb = (q.y - sy) * r;
+        t0 = fmaxf(t0, fminf(ta, tb));
+        t1 = fminf(t1, fmaxf(ta, tb));
+      } else {
+        miss = miss || !(p.y < sy && sy < q.y);
+      }
+      const float rz = rcp_approx(dz);  // the spot is at z = 0, dz > 0
+      t0 = fmaxf(t0, p.z * rz);
+      t1 = fminf(t1, q.z * rz);
+      if (!miss && t1 - t0 > o.eta) return false;
+    }
+  }
+  return true;
+}
+
 template <int SCAN, int COS, int MODE>
 __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair* blkp, uint32_t n,
                                               int warp_rel, int n_warps, const TileState& ts,
                                               uint32_t col_addr, FwdCount& cnt,
-                                              int mom_J = 0) {
+                                              int mom_J = 0, const OccSet* occ = nullptr) {
   const float2 kbin2 = make_float2(a.kbin, a.kbin);
   const float2 magic2 = make_float2(kMagic, kMagic);
   const float2 ikbin_neg = make_float2(-1.0f / a.kbin, -1.0f / a.kbin);
@@ -543,8 +593,19 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
 #endif
     } else {
       const float2 t = __fadd2_rd(u, magic2);  // kMagic + floor(u), exactly
-      const uint32_t ba = (uint32_t)(__float_as_int(t.x) - kMagicBits);
-      const uint32_t bb = (uint32_t)(__float_as_int(t.y) - kMagicBits);
+      uint32_t ba = (uint32_t)(__float_as_int(t.x) - kMagicBits);
+      uint32_t bb = (uint32_t)(__float_as_int(t.y) - kMagicBits);
+      if (MODE == MODE_NEAREST_OCC) {
+        // visibility only for pairs that would be binned; a hidden pair's bin
+        // is moved out of range, so its reduction is predicated off
+        const float sx = ts.sx2.x, sy = ts.sy2.x;
+        if (ba < (uint32_t)ts.lim && facing<COS>(cn.x) &&
+            !occ_seen(*occ, sx, sy, q.px.x - sx, q.py.x - sy, sqrt_approx(q.pz2.x), r2.x))
+          ba = 0xFFFFFFFFu;
+        if (bb < (uint32_t)ts.lim && facing<COS>(cn.y) &&
+            !occ_seen(*occ, sx, sy, q.px.y - sx, q.py.y - sy, sqrt_approx(q.pz2.y), r2.y))
+          bb = 0xFFFFFFFFu;
+      }
       const uint32_t aa = col_addr + ba * (kTile * 4);
       const uint32_t ab = col_addr + bb * (kTile * 4);
       // the in-window and facing test and the reduction in one predicated
@@ -723,7 +784,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
                            const FwdSmem& sm, int stages, FwdCount& cnt, const MomTab* mt,
                            uint32_t& it, unsigned long long* chunk_counter = nullptr,
                            unsigned long long chunk = 0, unsigned long long units_total = 0,
-                           uint32_t max_claims = 0) {
+                           uint32_t max_claims = 0, const OccSet* occ = nullptr) {
   const int mom_J = (MODE == MODE_SPLAT_MOM) ? mt->J : 0;
   const uint32_t hist_words = (MODE == MODE_SPLAT_MOM) ? (uint32_t)kMoments * kMomRows * kTile
                                                        : a.bw * kTile;
@@ -861,7 +922,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         const uint32_t first = blk * a.ppb;
         compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb,
                                        min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
-                                       cnt, mom_J);
+                                       cnt, mom_J, occ);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);

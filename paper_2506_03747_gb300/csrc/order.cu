@@ -53,11 +53,13 @@ __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* curso
 __global__ void pack_perm_kernel(const float* __restrict__ raw, uint64_t P, int scan_mode,
                                  int cos_mode, double lx, double ly, double inv_cdt,
                                  const uint32_t* __restrict__ perm, PointPair* pairs,
-                                 unsigned int* err) {
+                                 unsigned int* err, const __grid_constant__ OccSet occ) {
   const uint64_t n_pairs = (P + 1) / 2;
+  // only the laser leg of a non-confocal scan is tested here
+  const OccSet* o = (occ.n > 0 && scan_mode == NLOS_NONCONFOCAL) ? &occ : nullptr;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs;
        k += (uint64_t)gridDim.x * blockDim.x)
-    pack_pair(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, pairs, err, perm);
+    pack_pair(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, pairs, err, perm, o);
 }
 
 __global__ void bounds_kernel(const float* __restrict__ raw, uint64_t P, int scan_mode,
@@ -95,7 +97,8 @@ cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st) {
   const uint64_t n_pairs = (P + 1) / 2;
   const double lx = s.params.laser_x, ly = s.params.laser_y, inv_cdt = 1.0 / g.cdt;
   pack_perm_kernel<<<grid_for(n_pairs, 256, s.num_sms), 256, 0, st>>>(
-      s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.pairs, &s.scratch->err);
+      s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.pairs, &s.scratch->err,
+      s.occ);
   const uint64_t n_sub = (n_pairs + kSubPairs - 1) / kSubPairs;
   bounds_kernel<<<grid_for(n_sub, 8, s.num_sms), 256, 0, st>>>(
       s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.bounds, n_sub);

@@ -7,6 +7,38 @@
 
 namespace nlos {
 
+// Part of the segment z -> x strictly inside occluder k of o, in units of the
+// segment (FP64; the pack step's laser-leg visibility test).
+__device__ inline double occ_chord64(const OccSet& o, int k, const double z[3],
+                                     const double x[3]) {
+  const float4 p = o.occ[2 * k], q = o.occ[2 * k + 1];
+  const double d[3] = {x[0] - z[0], x[1] - z[1], x[2] - z[2]};
+  double t0 = 0.0, t1 = 1.0;
+  if (p.w == 0.f) {
+    const double f[3] = {z[0] - (double)p.x, z[1] - (double)p.y, z[2] - (double)p.z};
+    const double A = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double B = f[0] * d[0] + f[1] * d[1] + f[2] * d[2];
+    const double C = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] - (double)q.x * (double)q.x;
+    const double disc = B * B - A * C;
+    if (!(A > 0.0) || !(disc > 0.0)) return 0.0;
+    const double sq = sqrt(disc);
+    t0 = fmax(t0, (-B - sq) / A);
+    t1 = fmin(t1, (-B + sq) / A);
+  } else {
+    const double lo[3] = {p.x, p.y, p.z}, hi[3] = {q.x, q.y, q.z};
+    for (int c = 0; c < 3; ++c) {
+      if (d[c] == 0.0) {
+        if (!(lo[c] < z[c] && z[c] < hi[c])) return 0.0;
+        continue;
+      }
+      const double ta = (lo[c] - z[c]) / d[c], tb = (hi[c] - z[c]) / d[c];
+      t0 = fmax(t0, fmin(ta, tb));
+      t1 = fmin(t1, fmax(ta, tb));
+    }
+  }
+  return t1 > t0 ? t1 - t0 : 0.0;
+}
+
 // Packs point pairs (FP64 arithmetic on the device, FP32 storage) and checks
 // every point: finite values, z > 0, area > 0, albedo >= 0, |n| = 1 within 1e-3.
 //   confocal:     OBJECT: (na, nb, nc) = -sqrt(q) * (nx, ny, nz z);
@@ -16,11 +48,14 @@ namespace nlos {
 //                 NONE: kq = q / r_l^2; uoff = r_l / (c dt).
 // q = albedo * area.
 // perm (nullable): packed position -> index of the point in raw.
+// occ (nullable): occluders; non-confocal points hidden from the laser spot
+// (a chord above occ->eta) get no weight.
 __device__ __forceinline__ PointPair pack_pair_value(const float* __restrict__ raw, uint64_t P,
                                                      uint64_t k, int scan_mode, int cos_mode,
                                                      double lx, double ly, double inv_cdt,
                                                      unsigned int* err,
-                                                     const uint32_t* __restrict__ perm) {
+                                                     const uint32_t* __restrict__ perm,
+                                                     const OccSet* occ = nullptr) {
   float f[2][8];
   for (int h = 0; h < 2; ++h) {
     const uint64_t i = 2 * k + h;
@@ -46,7 +81,15 @@ __device__ __forceinline__ PointPair pack_pair_value(const float* __restrict__ r
         const double rl = sqrt(vx * vx + vy * vy + vz * vz);
         const double cl = -(nx * vx + ny * vy + nz * vz) / rl;
         uoff = rl * inv_cdt;
-        if (cos_mode == NLOS_COS_NONE) kq = q / (rl * rl);
+        bool lit = true;
+        if (occ) {
+          const double zl[3] = {lx, ly, 0.0}, xp[3] = {x, y, z};
+          for (int k = 0; k < occ->n; ++k)
+            if (occ_chord64(*occ, k, zl, xp) > (double)occ->eta) lit = false;
+        }
+        if (!lit) {
+          // no weight; kq = s = 0 below
+        } else if (cos_mode == NLOS_COS_NONE) kq = q / (rl * rl);
         else if (cos_mode == NLOS_COS_OBJECT) s = q * (cl > 0 ? cl : 0.0) / (rl * rl);
         else s = q * (cl > 0 ? cl : 0.0) / (rl * rl) * (z / rl) * z;
       }
@@ -79,8 +122,9 @@ __device__ __forceinline__ PointPair pack_pair_value(const float* __restrict__ r
 __device__ __forceinline__ void pack_pair(const float* __restrict__ raw, uint64_t P, uint64_t k,
                                           int scan_mode, int cos_mode, double lx, double ly,
                                           double inv_cdt, PointPair* pairs, unsigned int* err,
-                                          const uint32_t* __restrict__ perm = nullptr) {
-  pairs[k] = pack_pair_value(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, err, perm);
+                                          const uint32_t* __restrict__ perm = nullptr,
+                                          const OccSet* occ = nullptr) {
+  pairs[k] = pack_pair_value(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, err, perm, occ);
 }
 
 // Bounds of sub-block sb (points 2 kSubPairs sb .. in packed order) by one

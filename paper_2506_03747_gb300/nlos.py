@@ -107,6 +107,7 @@ def load(path: str | None = None):
                                      ctypes.POINTER(_U64)]),
             "nlos_simulate": (S, [_P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
             "nlos_scene_set_points": (S, [_P, _P, _U64, ctypes.c_int, _P]),
+            "nlos_scene_set_occluders": (S, [_P, _P, _U32, _P]),
             "nlos_scene_check": (S, [_P, _P]),
             "nlos_forward": (S, [_P, _P, _P]),
             "nlos_detect": (S, [_P, _P, _P, _P, _P]),
@@ -279,6 +280,17 @@ def scene_set_points(scene: Scene, points, stream=None):
     n = points.shape[0]
     _check(_lib.nlos_scene_set_points(scene.handle, _ptr(points) if n else None, n, on_dev,
                                       _stream(stream)))
+
+
+def scene_set_occluders(scene: Scene, occluders, stream=None):
+    """Occluder records [n, 8] (kind, a0, a1, a2, b0, b1, b2, unused; kind 0 =
+    sphere with centre a and radius b0, kind 1 = box with corners a < b), host
+    memory; None or an empty array removes them."""
+    rec = np.ascontiguousarray(np.zeros((0, 8)) if occluders is None else occluders,
+                               dtype=np.float32).reshape(-1, 8)
+    n = rec.shape[0]
+    _check(_lib.nlos_scene_set_occluders(scene.handle, rec.ctypes.data if n else None, n,
+                                         _stream(stream)))
 
 
 def scene_check(scene: Scene, stream=None):

@@ -184,6 +184,22 @@ def primitive_union_points(rng, n_points: int):
     return _pack(pos, nrm, albedo, np.full(n_points, area)), prims
 
 
+def occluder_records(prims) -> np.ndarray:
+    """The primitives of a union as occluder records [n, 8] (float32): kind 0
+    sphere (centre, radius), kind 1 box (lower corner, upper corner)."""
+    out = np.zeros((len(prims), 8), dtype=np.float32)
+    for i, pr in enumerate(prims):
+        if pr[0] == "sphere":
+            out[i, 0] = 0
+            out[i, 1:4] = pr[1]
+            out[i, 4] = pr[2]
+        else:
+            out[i, 0] = 1
+            out[i, 1:4] = pr[1]
+            out[i, 4:7] = pr[2]
+    return out
+
+
 def workload_union64(seed: int = SEED_BASE + 2, n_points: int = 262144):
     """The acquisition window starts at the earliest object round trip seen
     from the wall centre (2 * stand-off + 2 * 0.3 m), so that it covers the
