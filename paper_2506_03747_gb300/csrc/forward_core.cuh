@@ -495,10 +495,12 @@ __device__ __forceinline__ void red_moments(uint32_t addr, float w, float c, uin
 // chord in units of A (no division), from |S + t d - c|^2 < r^2; boxes: the
 // slab intervals of t, with reciprocal estimates. The threshold is far above
 // the FP32 rounding of the chord except for near-tangent segments, which the
-// parity tests treat like pairs near a bin edge.
-__device__ __forceinline__ bool occ_seen(const OccSet& o, float sx, float sy, float dx, float dy,
-                                         float dz, float A) {
-  for (int k = 0; k < o.n; ++k) {
+// parity tests treat like pairs near a bin edge. Only the occluders of `mask`
+// (those the unit's segments can meet, occ_unit_mask) are tested.
+__device__ __forceinline__ bool occ_seen(const OccSet& o, uint32_t mask, float sx, float sy,
+                                         float dx, float dy, float dz, float A) {
+  for (; mask; mask &= mask - 1) {
+    const int k = __ffs(mask) - 1;
     const float4 p = o.occ[2 * k], q = o.occ[2 * k + 1];
     if (p.w == 0.f) {
       const float fx = sx - p.x, fy = sy - p.y;
@@ -542,7 +544,8 @@ template <int SCAN, int COS, int MODE>
 __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair* blkp, uint32_t n,
                                               int warp_rel, int n_warps, const TileState& ts,
                                               uint32_t col_addr, FwdCount& cnt,
-                                              int mom_J = 0, const OccSet* occ = nullptr) {
+                                              int mom_J = 0, const OccSet* occ = nullptr,
+                                              uint32_t occ_mask = 0) {
   const float2 kbin2 = make_float2(a.kbin, a.kbin);
   const float2 magic2 = make_float2(kMagic, kMagic);
   const float2 ikbin_neg = make_float2(-1.0f / a.kbin, -1.0f / a.kbin);
@@ -600,10 +603,12 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
         // is moved out of range, so its reduction is predicated off
         const float sx = ts.sx2.x, sy = ts.sy2.x;
         if (ba < (uint32_t)ts.lim && facing<COS>(cn.x) &&
-            !occ_seen(*occ, sx, sy, q.px.x - sx, q.py.x - sy, sqrt_approx(q.pz2.x), r2.x))
+            !occ_seen(*occ, occ_mask, sx, sy, q.px.x - sx, q.py.x - sy, sqrt_approx(q.pz2.x),
+                      r2.x))
           ba = 0xFFFFFFFFu;
         if (bb < (uint32_t)ts.lim && facing<COS>(cn.y) &&
-            !occ_seen(*occ, sx, sy, q.px.y - sx, q.py.y - sy, sqrt_approx(q.pz2.y), r2.y))
+            !occ_seen(*occ, occ_mask, sx, sy, q.px.y - sx, q.py.y - sy, sqrt_approx(q.pz2.y),
+                      r2.y))
           bb = 0xFFFFFFFFu;
       }
       const uint32_t aa = col_addr + ba * (kTile * 4);
@@ -712,14 +717,8 @@ __device__ __forceinline__ float imax(float a0, float a1, float b0, float b1) {
 // against the window with `margin` bins on each side, the object cosine
 // (upper bound of n.(spot - x) over the boxes) and whether any point carries
 // weight. Conservative: a unit it keeps may still bin nothing.
-template <int SCAN, int COS>
-__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin) {
-  const unsigned long long tw = unit / a.n_blk;
-  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
-  const uint32_t tile = (uint32_t)(tw / a.n_win);
-  const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
-  const float lim = (float)min(a.bw, a.B - w0);
-  const TileBound t = a.tiles[tile];
+// Bounds of point block blk: the union of its sub-blocks' bounds.
+__device__ __forceinline__ BlockBound block_bound(const FwdArgs& a, uint32_t blk) {
   const uint32_t sub_per = a.ppb / kSubPairs;
   const uint32_t sb0 = blk * sub_per;
   const uint32_t n_sub = (a.n_pairs + kSubPairs - 1) / kSubPairs;
@@ -735,6 +734,18 @@ __device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long u
     b.uo0 = fminf(b.uo0, c.uo0); b.uo1 = fmaxf(b.uo1, c.uo1);
     b.live = fmaxf(b.live, c.live);
   }
+  return b;
+}
+
+template <int SCAN, int COS>
+__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin) {
+  const unsigned long long tw = unit / a.n_blk;
+  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
+  const uint32_t tile = (uint32_t)(tw / a.n_win);
+  const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
+  const float lim = (float)min(a.bw, a.B - w0);
+  const TileBound t = a.tiles[tile];
+  const BlockBound b = block_bound(a, blk);
   if (b.live == 0.f) return false;
   const float dx = fmaxf(0.f, fmaxf(b.x0 - t.sx1, t.sx0 - b.x1));
   const float dy = fmaxf(0.f, fmaxf(b.y0 - t.sy1, t.sy0 - b.y1));
@@ -757,6 +768,47 @@ __device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long u
   }
   return true;
 }
+
+// Occluders that can meet a segment from a spot of the unit's tile (z = 0)
+// to a point of its block, as bits (conservative). A segment ending at depth
+// z_p in [z0, z1] is at depth zeta at t = zeta / z_p, over the lateral box
+// interpolated at t between the tile's spot box and the block's box; over
+// the depths an occluder spans, t stays in [zeta_lo / z1, min(1, zeta_hi /
+// z0)], and the box is linear in t, so its extremes sit at those two ends.
+// Without bounds every occluder counts.
+__device__ __forceinline__ uint32_t occ_unit_mask(const FwdArgs& a, unsigned long long unit,
+                                                  const OccSet& o) {
+  const uint32_t all = o.n >= 32 ? 0xFFFFFFFFu : (1u << o.n) - 1u;
+  if (a.bounds == nullptr) return all;
+  const unsigned long long tw = unit / a.n_blk;
+  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
+  const TileBound t = a.tiles[(uint32_t)(tw / a.n_win)];
+  const BlockBound b = block_bound(a, blk);
+  if (!(b.z0 > 0.f)) return all;
+  constexpr float pad = 1e-4f;  // metres, against rounding of the boxes
+  uint32_t m = 0;
+  for (int k = 0; k < o.n; ++k) {
+    const float4 p = o.occ[2 * k], q = o.occ[2 * k + 1];
+    const bool sph = p.w == 0.f;
+    const float ox0 = (sph ? p.x - q.x : p.x) - pad, ox1 = (sph ? p.x + q.x : q.x) + pad;
+    const float oy0 = (sph ? p.y - q.x : p.y) - pad, oy1 = (sph ? p.y + q.x : q.y) + pad;
+    const float oz0 = (sph ? p.z - q.x : p.z) - pad, oz1 = (sph ? p.z + q.x : q.z) + pad;
+    const float zlo = fmaxf(oz0, 0.f), zhi = fminf(oz1, b.z1);
+    if (zlo > zhi) continue;
+    const float tlo = zlo / b.z1, thi = fminf(1.f, zhi / b.z0);
+    const float xmin = fminf(fmaf(tlo, b.x0 - t.sx0, t.sx0), fmaf(thi, b.x0 - t.sx0, t.sx0));
+    const float xmax = fmaxf(fmaf(tlo, b.x1 - t.sx1, t.sx1), fmaf(thi, b.x1 - t.sx1, t.sx1));
+    const float ymin = fminf(fmaf(tlo, b.y0 - t.sy0, t.sy0), fmaf(thi, b.y0 - t.sy0, t.sy0));
+    const float ymax = fmaxf(fmaf(tlo, b.y1 - t.sy1, t.sy1), fmaf(thi, b.y1 - t.sy1, t.sy1));
+    if (xmax < ox0 || xmin > ox1 || ymax < oy0 || ymin > oy1) continue;
+    m |= 1u << k;
+  }
+  return m;
+}
+
+// Units carry the occluder mask of MODE_NEAREST_OCC in their top bits.
+constexpr int kUnitBits = 48;
+constexpr unsigned long long kUnitMask = (1ull << kUnitBits) - 1ull;
 
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -856,7 +908,10 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
             failed = true;
             break;
           }
-          unit_of[slot] = cur + j;
+          unsigned long long tag = cur + j;
+          if (MODE == MODE_NEAREST_OCC)
+            tag |= (unsigned long long)occ_unit_mask(a, cur + j, *occ) << kUnitBits;
+          unit_of[slot] = tag;
           fence_proxy_async_smem();
           issue_block(a, sm, cur + j, slot);
           ++k;
@@ -904,7 +959,8 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         }
         break;
       }
-      const unsigned long long unit = *(volatile unsigned long long*)&unit_of[slot];
+      const unsigned long long tag = *(volatile unsigned long long*)&unit_of[slot];
+      const unsigned long long unit = tag == kNoUnit ? kNoUnit : (tag & kUnitMask);
       if (unit != kNoUnit) {
         const long long tw = (long long)(unit / a.n_blk);
         const uint32_t blk = (uint32_t)(unit - (unsigned long long)tw * a.n_blk);
@@ -922,7 +978,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         const uint32_t first = blk * a.ppb;
         compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb,
                                        min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
-                                       cnt, mom_J, occ);
+                                       cnt, mom_J, occ, (uint32_t)(tag >> kUnitBits));
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
