@@ -14,7 +14,7 @@
 //   2. cell: each point's cell and the cell counts,
 //   3. scan: exclusive prefix sum of the counts (one CTA),
 //   4. scatter: perm[slot] = point, slot from the cell's cursor,
-//   5. pack (pack_pair through perm) and block bounds (one warp per block).
+//   5. pack (pack_pair through perm) and block bounds, one CTA per sub-block.
 #include "common.cuh"
 #include "order_core.cuh"
 #include "pack_core.cuh"
@@ -42,7 +42,7 @@ __global__ void cell_kernel(const float* __restrict__ raw, uint64_t P, const uin
 
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* counts) {
   __shared__ uint32_t wsum[32];
-  scan_cells(counts, wsum);
+  scan_cells<true>(counts, wsum);
 }
 
 __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* cursor, uint32_t* perm) {
@@ -50,26 +50,50 @@ __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* curso
                 (uint64_t)gridDim.x * blockDim.x, cursor, perm);
 }
 
-__global__ void pack_perm_kernel(const float* __restrict__ raw, uint64_t P, int scan_mode,
-                                 int cos_mode, double lx, double ly, double inv_cdt,
-                                 const uint32_t* __restrict__ perm, PointPair* pairs,
-                                 unsigned int* err, const __grid_constant__ OccSet occ) {
+// One CTA of kSubPairs threads per sub-block: thread k packs pair k of the
+// sub-block, and the CTA reduces the bounds of its 2 kSubPairs points (the
+// same per-point quantities as block_bound_warp).
+__global__ void __launch_bounds__(kSubPairs) pack_bounds_kernel(
+    const float* __restrict__ raw, uint64_t P, int scan_mode, int cos_mode, double lx, double ly,
+    double inv_cdt, const uint32_t* __restrict__ perm, PointPair* pairs, unsigned int* err,
+    BlockBound* bounds, const __grid_constant__ OccSet occ) {
+  static_assert(kSubPairs % 32 == 0 && kSubPairs <= 1024, "one thread per pair of a sub-block");
+  __shared__ float red[kSubPairs / 32][15];
   const uint64_t n_pairs = (P + 1) / 2;
+  const uint64_t k = (uint64_t)blockIdx.x * kSubPairs + threadIdx.x;
   // only the laser leg of a non-confocal scan is tested here
   const OccSet* o = (occ.n > 0 && scan_mode == NLOS_NONCONFOCAL) ? &occ : nullptr;
-  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs;
-       k += (uint64_t)gridDim.x * blockDim.x)
+  float lo[7], hi[7], live = 0.f;
+  for (int c = 0; c < 7; ++c) {
+    lo[c] = 3.0e38f;
+    hi[c] = -3.0e38f;
+  }
+  if (k < n_pairs) {
     pack_pair(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, pairs, err, perm, o);
-}
-
-__global__ void bounds_kernel(const float* __restrict__ raw, uint64_t P, int scan_mode,
-                              int cos_mode, double lx, double ly, double inv_cdt,
-                              const uint32_t* __restrict__ perm, BlockBound* bounds,
-                              uint64_t n_sub) {
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t sb = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sb < n_sub;
-       sb += warps)
-    block_bound_warp(raw, P, sb, scan_mode, cos_mode, lx, ly, inv_cdt, perm, bounds + sb);
+    for (uint64_t i = 2 * k; i < min(P, 2 * k + 2); ++i)
+      bound_point(raw + 8 * (perm ? (uint64_t)perm[i] : i), scan_mode, cos_mode, lx, ly, inv_cdt,
+                  lo, hi, live);
+  }
+  bound_warp_reduce(lo, hi, live);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    for (int c = 0; c < 7; ++c) {
+      red[warp][c] = lo[c];
+      red[warp][7 + c] = hi[c];
+    }
+    red[warp][14] = live;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kSubPairs / 32; ++w) {
+      for (int c = 0; c < 7; ++c) {
+        lo[c] = fminf(lo[c], red[w][c]);
+        hi[c] = fmaxf(hi[c], red[w][7 + c]);
+      }
+      live = fmaxf(live, red[w][14]);
+    }
+    bounds[blockIdx.x] = bound_record(lo, hi, live);
+  }
 }
 
 unsigned grid_for(uint64_t n, int per_block, int sms) {
@@ -96,12 +120,10 @@ cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st) {
   scatter_kernel<<<grid_for(P, 256, s.num_sms), 256, 0, st>>>(s.cell, P, counts, s.perm);
   const uint64_t n_pairs = (P + 1) / 2;
   const double lx = s.params.laser_x, ly = s.params.laser_y, inv_cdt = 1.0 / g.cdt;
-  pack_perm_kernel<<<grid_for(n_pairs, 256, s.num_sms), 256, 0, st>>>(
-      s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.pairs, &s.scratch->err,
-      s.occ);
   const uint64_t n_sub = (n_pairs + kSubPairs - 1) / kSubPairs;
-  bounds_kernel<<<grid_for(n_sub, 8, s.num_sms), 256, 0, st>>>(
-      s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.bounds, n_sub);
+  pack_bounds_kernel<<<(unsigned)n_sub, kSubPairs, 0, st>>>(
+      s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.pairs, &s.scratch->err,
+      s.bounds, s.occ);
   return cudaGetLastError();
 }
 

@@ -111,13 +111,20 @@ __device__ __forceinline__ void cell_range(const float* __restrict__ raw, uint64
 // counts[c] <- sum of counts[0..c). One CTA of exactly 1024 threads: warp w
 // scans cells [w * 1024, (w + 1) * 1024) 32 at a time (coalesced loads,
 // shuffle scans), then the 32 warp totals are scanned; wsum: 32 shared words.
+// PREFETCH loads a warp's 1024 counts into registers before the serial
+// carry chain (32 loads in flight instead of one at a time; 32 registers).
+template <bool PREFETCH = false>
 __device__ __forceinline__ void scan_cells(uint32_t* counts, uint32_t* wsum) {
   constexpr int kPerWarp = kOrderCells / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* seg = counts + (size_t)w * kPerWarp;
+  uint32_t pre[PREFETCH ? kPerWarp / 32 : 1];
+  if (PREFETCH) {
+#pragma unroll
+    for (int j = 0; j < kPerWarp / 32; ++j) pre[j] = seg[32 * j + lane];
+  }
   uint32_t carry = 0;
-  for (int j = 0; j < kPerWarp; j += 32) {
-    const uint32_t v = seg[j + lane];
+  auto step = [&](int j, uint32_t v) {
     uint32_t x = v;  // inclusive scan of the 32 values
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -125,6 +132,12 @@ __device__ __forceinline__ void scan_cells(uint32_t* counts, uint32_t* wsum) {
     }
     seg[j + lane] = carry + x - v;  // exclusive within the warp's segment
     carry += __shfl_sync(0xffffffffu, x, 31);
+  };
+  if (PREFETCH) {
+#pragma unroll
+    for (int j = 0; j < kPerWarp; j += 32) step(j, pre[j / 32]);
+  } else {
+    for (int j = 0; j < kPerWarp; j += 32) step(j, seg[j + lane]);
   }
   if (lane == 0) wsum[w] = carry;
   __syncthreads();

@@ -127,6 +127,47 @@ __device__ __forceinline__ void pack_pair(const float* __restrict__ raw, uint64_
   pairs[k] = pack_pair_value(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, err, perm, occ);
 }
 
+// The per-point quantities of the block bounds: position, normal, laser-leg
+// offset (non-confocal), and whether the point can carry weight.
+__device__ __forceinline__ void bound_point(const float* r, int scan_mode, int cos_mode, double lx,
+                                            double ly, double inv_cdt, float lo[7], float hi[7],
+                                            float& live) {
+  const float x = r[0], y = r[1], z = r[2];
+  float uo = 0.f;
+  bool w = r[6] * r[7] > 0.f;
+  if (scan_mode == NLOS_NONCONFOCAL) {
+    const double vx = x - lx, vy = y - ly, vz = z;
+    const double rl = sqrt(vx * vx + vy * vy + vz * vz);
+    uo = (float)(rl * inv_cdt);
+    if (cos_mode != NLOS_COS_NONE) w = w && -(r[3] * vx + r[4] * vy + r[5] * vz) > 0.0;
+  }
+  const float v[7] = {x, y, z, r[3], r[4], r[5], uo};
+  for (int c = 0; c < 7; ++c) {
+    lo[c] = fminf(lo[c], v[c]);
+    hi[c] = fmaxf(hi[c], v[c]);
+  }
+  if (w) live = 1.f;
+}
+
+__device__ __forceinline__ void bound_warp_reduce(float lo[7], float hi[7], float& live) {
+  for (int o = 16; o > 0; o >>= 1) {
+    for (int c = 0; c < 7; ++c) {
+      lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+      hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+    }
+    live = fmaxf(live, __shfl_xor_sync(0xffffffffu, live, o));
+  }
+}
+
+__device__ __forceinline__ BlockBound bound_record(const float lo[7], const float hi[7],
+                                                   float live) {
+  BlockBound b;
+  b.x0 = lo[0]; b.x1 = hi[0]; b.y0 = lo[1]; b.y1 = hi[1]; b.z0 = lo[2]; b.z1 = hi[2];
+  b.nx0 = lo[3]; b.nx1 = hi[3]; b.ny0 = lo[4]; b.ny1 = hi[4]; b.nz0 = lo[5]; b.nz1 = hi[5];
+  b.uo0 = lo[6]; b.uo1 = hi[6]; b.live = live; b.pad = 0.f;
+  return b;
+}
+
 // Bounds of sub-block sb (points 2 kSubPairs sb .. in packed order) by one
 // warp; lane 0 writes *out. Same per-point quantities as pack_pair.
 __device__ __forceinline__ void block_bound_warp(const float* __restrict__ raw, uint64_t P,
@@ -143,38 +184,11 @@ __device__ __forceinline__ void block_bound_warp(const float* __restrict__ raw, 
   float live = 0.f;
   const uint64_t first = sb * 2 * kSubPairs;
   const uint64_t last = min(P, first + 2 * kSubPairs);
-  for (uint64_t i = first + lane; i < last; i += 32) {
-    const float* r = raw + 8 * (perm ? (uint64_t)perm[i] : i);
-    const float x = r[0], y = r[1], z = r[2];
-    float uo = 0.f;
-    bool w = r[6] * r[7] > 0.f;
-    if (scan_mode == NLOS_NONCONFOCAL) {
-      const double vx = x - lx, vy = y - ly, vz = z;
-      const double rl = sqrt(vx * vx + vy * vy + vz * vz);
-      uo = (float)(rl * inv_cdt);
-      if (cos_mode != NLOS_COS_NONE) w = w && -(r[3] * vx + r[4] * vy + r[5] * vz) > 0.0;
-    }
-    const float v[7] = {x, y, z, r[3], r[4], r[5], uo};
-    for (int c = 0; c < 7; ++c) {
-      lo[c] = fminf(lo[c], v[c]);
-      hi[c] = fmaxf(hi[c], v[c]);
-    }
-    if (w) live = 1.f;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    for (int c = 0; c < 7; ++c) {
-      lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-      hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
-    }
-    live = fmaxf(live, __shfl_xor_sync(0xffffffffu, live, o));
-  }
-  if (lane == 0) {
-    BlockBound b;
-    b.x0 = lo[0]; b.x1 = hi[0]; b.y0 = lo[1]; b.y1 = hi[1]; b.z0 = lo[2]; b.z1 = hi[2];
-    b.nx0 = lo[3]; b.nx1 = hi[3]; b.ny0 = lo[4]; b.ny1 = hi[4]; b.nz0 = lo[5]; b.nz1 = hi[5];
-    b.uo0 = lo[6]; b.uo1 = hi[6]; b.live = live; b.pad = 0.f;
-    *out = b;
-  }
+  for (uint64_t i = first + lane; i < last; i += 32)
+    bound_point(raw + 8 * (perm ? (uint64_t)perm[i] : i), scan_mode, cos_mode, lx, ly, inv_cdt,
+                lo, hi, live);
+  bound_warp_reduce(lo, hi, live);
+  if (lane == 0) *out = bound_record(lo, hi, live);
 }
 
 }  // namespace nlos
