@@ -56,6 +56,11 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #ifndef NLOS_FWD_STAGES
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
 #endif
+#ifndef NLOS_FWD_UNROLL
+#define NLOS_FWD_UNROLL 4                   // standalone forward: unroll of the pair loop
+#endif
+
+constexpr int kFwdUnroll = NLOS_FWD_UNROLL;  // (#pragma unroll takes no macro)
 
 enum { MODE_NEAREST = 0, MODE_NEAREST_COUNT = 1, MODE_SPLAT = 2, MODE_SPLAT_MOM = 3,
        MODE_NEAREST_OCC = 4 /* NEAREST with the occluder visibility test */ };
@@ -540,7 +545,7 @@ __device__ __forceinline__ bool occ_seen(const OccSet& o, uint32_t mask, float s
   return true;
 }
 
-template <int SCAN, int COS, int MODE>
+template <int SCAN, int COS, int MODE, int UNROLL>
 __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair* blkp, uint32_t n,
                                               int warp_rel, int n_warps, const TileState& ts,
                                               uint32_t col_addr, FwdCount& cnt,
@@ -549,7 +554,7 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
   const float2 kbin2 = make_float2(a.kbin, a.kbin);
   const float2 magic2 = make_float2(kMagic, kMagic);
   const float2 ikbin_neg = make_float2(-1.0f / a.kbin, -1.0f / a.kbin);
-#pragma unroll 2
+#pragma unroll UNROLL
   for (uint32_t i = warp_rel; i < n; i += n_warps) {
     PointPair q;
     load_pair(blkp + i, q);
@@ -829,9 +834,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // pairs stopped by the early out) take more of them. Consumers
 // flush their (tile, window) histogram whenever the tile changes and at the
 // end. `it` carries the barrier phases across calls (the serving kernel runs
-// one call per work item). Every wait is bounded; returns false if one gave
-// up (the error is in *a.err).
-template <int SCAN, int COS, int MODE>
+// one call per work item). UNROLL: unroll of the consumers' pair loop (more
+// unrolling costs registers). Every wait is bounded; returns false if one
+// gave up (the error is in *a.err).
+template <int SCAN, int COS, int MODE, int UNROLL>
 __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
                            const FwdSmem& sm, int stages, FwdCount& cnt, const MomTab* mt,
                            uint32_t& it, unsigned long long* chunk_counter = nullptr,
@@ -976,7 +982,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
           named_barrier(1, nthr);
         }
         const uint32_t first = blk * a.ppb;
-        compute_block<SCAN, COS, MODE>(a, sm.stage + (size_t)slot * a.ppb,
+        compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb,
                                        min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
                                        cnt, mom_J, occ, (uint32_t)(tag >> kUnitBits));
       }
