@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   FwdCount cnt;
   uint32_t it = 0;
-  (void)fwd_run_ws<SCAN, COS, MODE, kFwdUnroll>(a, 0, 0, sm, (int)a.stages, cnt, &mt, it,
-                                                a.next_chunk, a.chunk, a.units, 0, &occ);
+  (void)fwd_run_ws<SCAN, COS, MODE, kFwdUnroll, true>(a, 0, 0, sm, (int)a.stages, cnt, &mt, it,
+                                                      a.next_chunk, a.chunk, a.units, 0, &occ);
   if (MODE == MODE_NEAREST_COUNT && cnt.boundary) atomicAdd(a.boundary, cnt.boundary);
   // the count is warp-uniform: one lane adds it, 64 pairs per warp iteration
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);

@@ -435,15 +435,19 @@ __device__ __forceinline__ void flush_quads(const FwdArgs& a, const float* hist,
 // window; four consecutive bins per thread, one vector reduction each. Runs
 // on the warps [w_first, w_first + n_warps) of the CTA. Radii up to 16 use
 // a compile-time unrolled convolution.
+// Only histogram rows [rlo, rhi) may be nonzero, so only the output bins
+// they reach are written.
 template <int MODE>
 __device__ __forceinline__ void flush_tile(const FwdArgs& a, long long tw, const float* hist,
-                                           int warp_rel, int n_warps) {
+                                           int warp_rel, int n_warps, int rlo, int rhi) {
   const uint32_t tile = (uint32_t)(tw / a.n_win);
   const uint32_t win = (uint32_t)(tw % a.n_win);
   const int w0 = (int)(win * a.bw);
   const int R = (MODE == MODE_SPLAT) ? 0 : a.R;
-  const int lo = max(0, w0 - R) & ~3;
-  const int hi = min((int)a.B, w0 + (int)a.bw + R);
+  if (rhi <= rlo) return;
+  const int lo = max(0, w0 + rlo - R) & ~3;
+  const int hi = min((int)a.B, w0 + rhi + R);
+  if (hi <= lo) return;
   const int nq = (hi - lo + 3) >> 2;  // quads of output bins
   const int c = threadIdx.x & 31;
   const uint32_t s = tile * kTile + c;
@@ -743,7 +747,8 @@ __device__ __forceinline__ BlockBound block_bound(const FwdArgs& a, uint32_t blk
 }
 
 template <int SCAN, int COS>
-__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin) {
+__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin,
+                                          float& ulo_out, float& uhi_out) {
   const unsigned long long tw = unit / a.n_blk;
   const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
   const uint32_t tile = (uint32_t)(tw / a.n_win);
@@ -764,6 +769,8 @@ __device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long u
     ulo += b.uo0;
     uhi += b.uo1;
   }
+  ulo_out = ulo;
+  uhi_out = uhi;
   if (uhi < -margin || ulo >= lim + margin) return false;
   if (COS != NLOS_COS_NONE) {
     const float f = imax(b.nx0, b.nx1, t.sx0 - b.x1, t.sx1 - b.x0) +
@@ -811,6 +818,16 @@ __device__ __forceinline__ uint32_t occ_unit_mask(const FwdArgs& a, unsigned lon
   return m;
 }
 
+// Histogram rows a unit can touch, packed lo | hi << 16, from its u range
+// (window-relative) widened by the mode's margin and two bins against
+// rounding, clipped to [0, bw).
+__device__ __forceinline__ uint32_t unit_rows(float ulo, float uhi, float margin, uint32_t bw) {
+  const float m = ceilf(margin) + 2.f;
+  const float lo = fmaxf(floorf(fmaxf(ulo, -1e6f)) - m, 0.f);
+  const float hi = fminf(ceilf(fminf(uhi, 1e6f)) + m + 1.f, (float)bw);
+  return lo < hi ? (uint32_t)lo | ((uint32_t)hi << 16) : 0u;
+}
+
 // Units carry the occluder mask of MODE_NEAREST_OCC in their top bits.
 constexpr int kUnitBits = 48;
 constexpr unsigned long long kUnitMask = (1ull << kUnitBits) - 1ull;
@@ -834,10 +851,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // pairs stopped by the early out) take more of them. Consumers
 // flush their (tile, window) histogram whenever the tile changes and at the
 // end. `it` carries the barrier phases across calls (the serving kernel runs
-// one call per work item). UNROLL: unroll of the consumers' pair loop (more
-// unrolling costs registers). Every wait is bounded; returns false if one
-// gave up (the error is in *a.err).
-template <int SCAN, int COS, int MODE, int UNROLL>
+// one call per work item). UNROLL: unroll of the consumers' pair loop;
+// RANGED: track the histogram rows each tile can touch (from the unit
+// bounds) and flush and zero only those (both cost registers). Every wait is
+// bounded; returns false if one gave up (the error is in *a.err).
+template <int SCAN, int COS, int MODE, int UNROLL, bool RANGED>
 __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned long long u1,
                            const FwdSmem& sm, int stages, FwdCount& cnt, const MomTab* mt,
                            uint32_t& it, unsigned long long* chunk_counter = nullptr,
@@ -848,6 +866,11 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
                                                        : a.bw * kTile;
   __shared__ int s_abort;
   __shared__ uint32_t s_used;  // slots this call used (units + the end mark)
+  // rows each lane's unit can touch (producer), and for each slot the rows
+  // its tile's units so far can touch (consumers)
+  constexpr int kMaxRangedStages = 8;
+  __shared__ uint32_t s_lane_rows[32];
+  __shared__ uint32_t s_slot_rows[kMaxRangedStages];
   float* hist = sm.hist;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -861,11 +884,14 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     s_used = 0;
   }
   __syncthreads();
+  const bool cull = NLOS_FWD_CULL && a.bounds != nullptr && MODE != MODE_NEAREST_COUNT;
+  // histogram rows tracked per tile (flush and zero only those); the moment
+  // histograms have their own layout and are always handled whole
+  const bool ranged = RANGED && cull && MODE != MODE_SPLAT_MOM && stages <= kMaxRangedStages;
   if (warp == 0) {
     // The whole warp walks the units 32 at a time: each lane tests one unit
     // against the bounds (unit_live), then lane 0 stages the live ones in
     // order. Chunk claims (lane 0) run one ahead of their use.
-    const bool cull = NLOS_FWD_CULL && a.bounds != nullptr && MODE != MODE_NEAREST_COUNT;
     const float margin = window_margin<MODE>(a, mom_J);
     unsigned long long cur = u0, lim = u1, next = 0;
     bool have_next = false;  // a chunk claimed ahead of its use
@@ -887,6 +913,8 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     }
     uint32_t k = 0;
     bool failed = false;
+    long long run_tw = -1;   // lane 0: tile of the last staged unit
+    uint32_t run_rows = 0;   // lane 0: union of the rows of that tile's staged units
     for (;;) {
       if (cur == lim && have_next) {
         cur = min(next * chunk, units_total);
@@ -899,7 +927,12 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
       }
       if (cur >= lim) break;
       const uint32_t n = (uint32_t)min(32ull, lim - cur);
-      const bool live = lane < n && (!cull || unit_live<SCAN, COS>(a, cur + lane, margin));
+      float ulo = 0.f, uhi = 0.f;
+      const bool live = lane < n && (!cull || unit_live<SCAN, COS>(a, cur + lane, margin, ulo, uhi));
+      if (ranged) {
+        s_lane_rows[lane] = live ? unit_rows(ulo, uhi, margin, a.bw) : 0u;
+        __syncwarp();
+      }
       uint32_t mask = __ballot_sync(0xffffffffu, live);
       if (lane == 0) {
         while (mask) {
@@ -917,6 +950,18 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
           unsigned long long tag = cur + j;
           if (MODE == MODE_NEAREST_OCC)
             tag |= (unsigned long long)occ_unit_mask(a, cur + j, *occ) << kUnitBits;
+          if (ranged) {
+            const long long utw = (long long)((cur + j) / a.n_blk);
+            const uint32_t ur = s_lane_rows[j];
+            if (utw != run_tw) {
+              run_tw = utw;
+              run_rows = ur;
+            } else {
+              run_rows = min(run_rows & 0xFFFFu, ur & 0xFFFFu) |
+                         (max(run_rows >> 16, ur >> 16) << 16);
+            }
+            s_slot_rows[slot] = run_rows;
+          }
           unit_of[slot] = tag;
           fence_proxy_async_smem();
           issue_block(a, sm, cur + j, slot);
@@ -953,6 +998,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     const int nthr = ncw * 32;
     const uint32_t col_addr = smem_addr(hist) + (uint32_t)lane * 4u;
     TileState ts;
+    uint32_t tile_rows = (uint32_t)a.bw << 16;  // rows of the current tile that may be nonzero
     for (uint32_t k = 0;; ++k) {
       const uint32_t g = it + k;
       const int slot = (int)(g % (uint32_t)stages);
@@ -974,13 +1020,20 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
           named_barrier(1, nthr);  // every consumer is done with the previous tile
           if (ts.tw >= 0) {
             if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
-            else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+            else flush_tile<MODE>(a, ts.tw, hist, cw, ncw, (int)(tile_rows & 0xFFFFu),
+                                  (int)(tile_rows >> 16));
             named_barrier(1, nthr);
           }
-          for (uint32_t i = tid - 32; i < hist_words; i += nthr) hist[i] = 0.f;
+          // zero what the previous tile may have written (everything the first
+          // time: the buffer may hold another item's data)
+          const uint32_t z0 = (ranged && ts.tw >= 0) ? (tile_rows & 0xFFFFu) * kTile : 0u;
+          const uint32_t z1 = (ranged && ts.tw >= 0) ? (tile_rows >> 16) * kTile : hist_words;
+          for (uint32_t i = z0 + tid - 32; i < z1; i += nthr) hist[i] = 0.f;
           load_tile(a, tw, lane, ts, SCAN == NLOS_CONFOCAL, window_margin<MODE>(a, mom_J));
           named_barrier(1, nthr);
         }
+        // the producer's running union for this tile, up to this unit
+        if (ranged) tile_rows = s_slot_rows[slot];
         const uint32_t first = blk * a.ppb;
         compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb,
                                        min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
@@ -993,7 +1046,8 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     named_barrier(1, nthr);
     if (ts.tw >= 0) {
       if (MODE == MODE_SPLAT_MOM) flush_tile_mom(a, *mt, ts.tw, hist, cw, ncw);
-      else flush_tile<MODE>(a, ts.tw, hist, cw, ncw);
+      else flush_tile<MODE>(a, ts.tw, hist, cw, ncw, (int)(tile_rows & 0xFFFFu),
+                            (int)(tile_rows >> 16));
     }
   }
   __syncthreads();

@@ -180,9 +180,11 @@ template <int SCAN, int COS, int MODE>
 __device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, const FwdSmem& sm,
                                                     uint32_t& it) {
   FwdCount cnt;
-  // pair loop unrolled twice: this kernel's other item kinds leave fewer registers
-  const bool ok = fwd_run_ws<SCAN, COS, MODE, 2>(a, 0, 0, sm, kServeStages, cnt, nullptr, it,
-                                              a.next_chunk, a.chunk, a.units, kFwdClaims);
+  // pair loop unrolled twice and whole-window flushes: this kernel's other
+  // item kinds leave fewer registers
+  const bool ok = fwd_run_ws<SCAN, COS, MODE, 2, false>(a, 0, 0, sm, kServeStages, cnt, nullptr,
+                                                     it, a.next_chunk, a.chunk, a.units,
+                                                     kFwdClaims);
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
   if ((threadIdx.x & 31) == 0 && cnt.tested) atomicAdd(a.pairs_tested, cnt.tested * 64ull);
   return ok;
