@@ -250,9 +250,15 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   unsigned long long grid = (unsigned long long)sc.num_sms * per_sm;
   if (grid > a.units) grid = a.units;
-  // about 8 chunks per CTA on average: fine enough to even out units whose
-  // cost differs (the early out), coarse enough to keep flushes rare
-  a.chunk = std::max<unsigned long long>(1, a.units / (grid * NLOS_FWD_CHUNKS_PER_CTA));
+  // chunks of units claimed by the CTAs: about NLOS_FWD_CHUNKS_PER_CTA per
+  // CTA, but at least 8 units (a chunk mostly ends in a tile change, whose
+  // flush is worth amortising) and at most 64 (finer claims even out the
+  // cost of units, which the bounds do not predict), and never so large that
+  // some CTA would get none. Measured on the union (32768 units: 8 beats
+  // 6.7 per chunk) and heightfield (524288 units: 64 beats 108) workloads.
+  const unsigned long long per_cta = a.units / (grid * NLOS_FWD_CHUNKS_PER_CTA);
+  a.chunk = std::min<unsigned long long>(std::min<unsigned long long>(std::max<unsigned long long>(per_cta, 8), 64),
+                                         std::max<unsigned long long>(1, a.units / grid));
   fn<<<(unsigned)grid, threads, smem, st>>>(a, mt, sc.occ);
   return cudaGetLastError();
 }

@@ -180,9 +180,9 @@ template <int SCAN, int COS, int MODE>
 __device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, const FwdSmem& sm,
                                                     uint32_t& it) {
   FwdCount cnt;
-  // pair loop unrolled twice and whole-window flushes: this kernel's other
-  // item kinds leave fewer registers
-  const bool ok = fwd_run_ws<SCAN, COS, MODE, 2, false>(a, 0, 0, sm, kServeStages, cnt, nullptr,
+  // whole-window flushes: the row tracking's static shared memory would not
+  // fit beside this kernel's dynamic shared memory
+  const bool ok = fwd_run_ws<SCAN, COS, MODE, 4, false>(a, 0, 0, sm, kServeStages, cnt, nullptr,
                                                      it, a.next_chunk, a.chunk, a.units,
                                                      kFwdClaims);
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
@@ -306,18 +306,29 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
   __shared__ WorkItem s_item;
   __shared__ unsigned long long s_idx;
   __shared__ int s_lane;  // ring of the claimed item
+  // State that thread 0 alone uses, and the descriptor cache, in shared
+  // memory: kept in registers it would be live in every thread across the
+  // forward items, whose unrolled loop needs all 64.
+  struct LoopState {
+    unsigned long long tail_seen;  // last main-ring tail read from host memory
+    unsigned long long cyc[3];     // waiting, FORWARD items, other items
+    long long t_mark;
+    uint32_t cached_job, cached_gen;
+  };
+  __shared__ LoopState st;
 
   const int tid = threadIdx.x;
   if (tid == 0) {
     init_stage_barriers(sm.bars);
     atomicAdd_system(&q.ctl->alive, 1);
+    st.tail_seen = 0;
+    st.cyc[0] = st.cyc[1] = st.cyc[2] = 0;
+    st.t_mark = clock64();
+    st.cached_job = 0xFFFFFFFFu;
+    st.cached_gen = 0;
   }
   __syncthreads();
   uint32_t it = 0;
-  uint32_t cached_job = 0xFFFFFFFFu, cached_gen = 0;
-  unsigned long long tail_seen = 0;  // thread 0: last tail read from host memory
-  unsigned long long cyc_wait = 0, cyc_fwd = 0, cyc_other = 0;  // thread 0
-  long long t_mark = clock64();
 
   for (;;) {
     if (tid == 0) {
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
           xh = seen;
         }
         if (got != kNone) break;
-        if (h < tail_seen) {
+        if (h < st.tail_seen) {
           const unsigned long long seen = atomicCAS(q.head, h, h + 1);
           if (seen == h) {
             got = h;
@@ -353,8 +364,8 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
           h = seen;  // another CTA moved the head: retry from there
           continue;
         }
-        tail_seen = ld_acquire_sys(&q.ctl->tail[0]);
-        if (h < tail_seen) continue;
+        st.tail_seen = ld_acquire_sys(&q.ctl->tail[0]);
+        if (h < st.tail_seen) continue;
         if (ld_volatile_u32(&q.ctl->park)) break;
         if (clock64() - t0 > kIdleCycles) break;
         __nanosleep(500);
@@ -380,8 +391,8 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       s_idx = got;
       s_lane = lane;
       const long long now = clock64();
-      cyc_wait += (unsigned long long)(now - t_mark);
-      t_mark = now;
+      st.cyc[0] += (unsigned long long)(now - st.t_mark);
+      st.t_mark = now;
     }
     __syncthreads();
     const unsigned long long idx = s_idx;
@@ -394,17 +405,23 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       __syncthreads();
       continue;
     }
-    const WorkItem item = s_item;
+    // the item is read from shared memory where it is used (s_item changes
+    // only at the next claim, after the barrier that ends this item)
+    const WorkItem& item = s_item;
     // job descriptor: mapped memory -> shared memory, unless this CTA holds
     // it already (consecutive items mostly belong to one request; a slot's
-    // descriptor only changes with a new request, i.e. a new gen)
-    if (item.job != cached_job || item.gen != cached_gen) {
+    // descriptor only changes with a new request, i.e. a new gen). Every
+    // thread reads the cache tags before thread 0 updates them, after the
+    // barrier.
+    if (item.job != st.cached_job || item.gen != st.cached_gen) {
       const int4* src = reinterpret_cast<const int4*>(q.jobs + item.job);
       int4* dst = reinterpret_cast<int4*>(jd);
       for (int i = tid; i < (int)(sizeof(JobDesc) / 16); i += blockDim.x) dst[i] = src[i];
-      cached_job = item.job;
-      cached_gen = item.gen;
       __syncthreads();
+      if (tid == 0) {
+        st.cached_job = item.job;
+        st.cached_gen = item.gen;
+      }
     }
     switch (item.kind) {
       case K_BOX:  // the histogram's shared memory is free between forward items
@@ -456,16 +473,13 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
       atomicAdd_system(&q.status[item.job].done[phase_of(item.kind)], 1u);
       atomicAdd_system(reinterpret_cast<unsigned long long*>(&q.ctl->completed[s_lane]), 1ull);
       const long long now = clock64();
-      if (item.kind == K_FWD) cyc_fwd += (unsigned long long)(now - t_mark);
-      else cyc_other += (unsigned long long)(now - t_mark);
-      t_mark = now;
+      st.cyc[item.kind == K_FWD ? 1 : 2] += (unsigned long long)(now - st.t_mark);
+      st.t_mark = now;
     }
   }
   if (tid == 0) {
-    cyc_wait += (unsigned long long)(clock64() - t_mark);
-    atomicAdd_system(&q.ctl->cycles[0], cyc_wait);
-    atomicAdd_system(&q.ctl->cycles[1], cyc_fwd);
-    atomicAdd_system(&q.ctl->cycles[2], cyc_other);
+    st.cyc[0] += (unsigned long long)(clock64() - st.t_mark);
+    for (int k = 0; k < 3; ++k) atomicAdd_system(&q.ctl->cycles[k], st.cyc[k]);
     atomicSub_system(&q.ctl->alive, 1);
   }
 }
