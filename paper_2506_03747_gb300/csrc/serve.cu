@@ -108,6 +108,7 @@ constexpr uint64_t kXWindowPerSm = 32;       // express-ring items outstanding p
 constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
 constexpr uint64_t kNoiseChunk = 1ull << 13; // bins per NOISE item
 constexpr long long kIdleCycles = 2000000000LL;  // ~1 s without work: exit
+constexpr long long kXtailCycles = 40000;        // ~20 us: express tail refresh while busy
 constexpr int kServeThreads = 1024;           // 1 producer + 31 consumer warps (as the forward)
 constexpr int kServeStages = 3;               // staged point blocks in flight
 constexpr uint64_t kNone = ~0ull;
@@ -311,6 +312,8 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
   // forward items, whose unrolled loop needs all 64.
   struct LoopState {
     unsigned long long tail_seen;  // last main-ring tail read from host memory
+    unsigned long long xtail_seen; // last express-ring tail read from host memory
+    long long xtail_time;          // when it was read
     unsigned long long cyc[3];     // waiting, FORWARD items, other items
     long long t_mark;
     uint32_t cached_job, cached_gen;
@@ -322,6 +325,8 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
     init_stage_barriers(sm.bars);
     atomicAdd_system(&q.ctl->alive, 1);
     st.tail_seen = 0;
+    st.xtail_seen = 0;
+    st.xtail_time = 0;
     st.cyc[0] = st.cyc[1] = st.cyc[2] = 0;
     st.t_mark = clock64();
     st.cached_job = 0xFFFFFFFFu;
@@ -332,18 +337,25 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
 
   for (;;) {
     if (tid == 0) {
-      // claim the next published index: express ring first (its tail is
-      // read from host memory on every pass: the ring is mostly empty, and a
-      // stale tail would hold its items back), then the main ring by
-      // compare-and-swap on the device head against a cached tail (it only
-      // grows, so a stale value is a safe bound; the tail in host memory is
-      // read again only when the head has caught up with the cached value)
+      // claim the next published index: express ring first, then the main
+      // ring, each by compare-and-swap on its device head against a cached
+      // copy of its tail (tails only grow, so a stale value is a safe
+      // bound). The main tail is read again from host memory when the head
+      // has caught up with the cached value; the express tail on every pass
+      // while the main ring looks empty, else at most every kXtailCycles (so
+      // that 152 CTAs claiming short FORWARD items do not all read the same
+      // host cache line on every claim, which starved them)
       unsigned long long got = kNone;
       int lane = 0;
       const long long t0 = clock64();
       unsigned long long h = *reinterpret_cast<volatile unsigned long long*>(q.head);
       for (;;) {
-        const unsigned long long xt = ld_acquire_sys(&q.ctl->tail[1]);
+        const long long tnow = clock64();
+        if (!(h < st.tail_seen) || tnow - st.xtail_time > kXtailCycles) {
+          st.xtail_seen = ld_acquire_sys(&q.ctl->tail[1]);
+          st.xtail_time = tnow;
+        }
+        const unsigned long long xt = st.xtail_seen;
         unsigned long long xh = *reinterpret_cast<volatile unsigned long long*>(q.head + 1);
         while (xh < xt) {
           const unsigned long long seen = atomicCAS(q.head + 1, xh, xh + 1);
