@@ -94,15 +94,18 @@ constexpr uint64_t kZeroChunk = 1ull << 16;  // floats per ZERO item
 constexpr uint64_t kOrderChunk = 1ull << 13; // points per BOX / CELL / SCATTER item
 // FORWARD: a request's units are split into about kFwdChunksPerSm chunks per
 // SM (as the standalone launch splits them), at most kFwdMaxChunk units each;
-// each FORWARD item claims up to kFwdClaims chunks from the request's
-// counter, so that CTAs meeting cheap (culled) units take more of them, and
-// a CTA keeps its histogram across the units of one (tile, window) of a
-// chunk. The cap bounds an item (128 units of 32 scan points x 1024 points,
-// about 1 ms at most), and with it how long express items can wait for a
-// CTA when every CTA has just started a FORWARD item.
+// each FORWARD item claims chunks from the request's counter, one at a time,
+// so that CTAs meeting cheap (culled) units take more of them, and a CTA
+// keeps its histogram across the units of one (tile, window) of a chunk. An
+// item makes up to kFwdItemUnits / chunk claims (at least one): items of
+// about 256 units (32 scan points x 1024 points each; at most about 2 ms)
+// bound how long express items can wait for a CTA when every CTA has just
+// started a FORWARD item, while keeping the pipeline drain and the claim at
+// the end of each item rare. Work stays balanced at chunk granularity: an
+// item ends early once the counter is exhausted.
 constexpr uint64_t kFwdChunksPerSm = 32;
 constexpr uint64_t kFwdMaxChunk = 128;
-constexpr uint32_t kFwdClaims = 4;
+constexpr uint64_t kFwdItemUnits = 128;
 constexpr uint64_t kWindowPerSm = 16;        // main-ring items outstanding per SM (publication window)
 constexpr uint64_t kXWindowPerSm = 32;       // express-ring items outstanding per SM
 constexpr uint64_t kReduceChunk = 64;        // transients per REDUCE item
@@ -179,37 +182,38 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
 // One instance per (scan, cosine, bin mode).
 template <int SCAN, int COS, int MODE>
 __device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, const FwdSmem& sm,
-                                                    uint32_t& it) {
+                                                    uint32_t& it, uint32_t claims) {
   FwdCount cnt;
   // whole-window flushes: the row tracking's static shared memory would not
   // fit beside this kernel's dynamic shared memory
   const bool ok = fwd_run_ws<SCAN, COS, MODE, 4, false>(a, 0, 0, sm, kServeStages, cnt, nullptr,
                                                      it, a.next_chunk, a.chunk, a.units,
-                                                     kFwdClaims);
+                                                     claims);
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
   if ((threadIdx.x & 31) == 0 && cnt.tested) atomicAdd(a.pairs_tested, cnt.tested * 64ull);
   return ok;
 }
 
 template <int SCAN, int COS>
-__device__ bool fwd_item_cos(const FwdArgs& a, const FwdSmem& sm, uint32_t& it, int bin_mode) {
-  return bin_mode == NLOS_BIN_SPLAT ? fwd_item_mode<SCAN, COS, MODE_SPLAT>(a, sm, it)
-                                    : fwd_item_mode<SCAN, COS, MODE_NEAREST>(a, sm, it);
+__device__ bool fwd_item_cos(const FwdArgs& a, const FwdSmem& sm, uint32_t& it, int bin_mode,
+                             uint32_t cl) {
+  return bin_mode == NLOS_BIN_SPLAT ? fwd_item_mode<SCAN, COS, MODE_SPLAT>(a, sm, it, cl)
+                                    : fwd_item_mode<SCAN, COS, MODE_NEAREST>(a, sm, it, cl);
 }
 
-// FORWARD: up to kFwdClaims chunks of the job's units, claimed from its
-// counter (the item's range is unused).
-__device__ bool fwd_item(const JobDesc& j, const FwdSmem& sm, uint32_t& it) {
+// FORWARD: up to `cl` chunks of the job's units (the item's `end`), claimed
+// from its counter.
+__device__ bool fwd_item(const JobDesc& j, const FwdSmem& sm, uint32_t& it, uint32_t cl) {
   const FwdArgs& a = j.fwd;
   const int m = j.bin_mode;
   if (j.scan_mode == NLOS_CONFOCAL) {
-    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_NONE>(a, sm, it, m);
-    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, sm, it, m);
-    return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, sm, it, m);
+    if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_NONE>(a, sm, it, m, cl);
+    if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT>(a, sm, it, m, cl);
+    return fwd_item_cos<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(a, sm, it, m, cl);
   }
-  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, sm, it, m);
-  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, sm, it, m);
-  return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, sm, it, m);
+  if (j.cos_mode == NLOS_COS_NONE) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_NONE>(a, sm, it, m, cl);
+  if (j.cos_mode == NLOS_COS_OBJECT) return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(a, sm, it, m, cl);
+  return fwd_item_cos<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(a, sm, it, m, cl);
 }
 
 // REDUCE: transients [b, e) of the job, one warp per transient; the cube's
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(kServeThreads, 1) serve_kernel(const ServeArgs
         // a forward wait that gave up is recorded in the job error word; the
         // stage barriers are then out of step with the unit counter: start
         // them afresh (every copy has landed or been waited for, bounded)
-        if (!fwd_item(*jd, sm, it)) {
+        if (!fwd_item(*jd, sm, it, (uint32_t)item.end)) {
           if (tid == 0) {
             for (int i = 0; i < 2 * kServeStages; ++i) mbar_inval(&sm.bars[i]);
             init_stage_barriers(sm.bars);
@@ -798,12 +802,13 @@ void publish_phase(Server& sv, Request* r, int phase) {
     for (uint64_t b = 0; b < n; b += kZeroChunk)
       items.push_back({job, K_ZERO, gen, b, std::min<uint64_t>(n, b + kZeroChunk), 0});
   } else if (phase == PH_FWD) {
-    // enough items for every chunk to be claimed: each claims kFwdClaims
-    // chunks unless the counter has passed the last one
+    // enough items for every chunk to be claimed: each makes `claims`
+    // claims (its `end`) unless the counter has passed the last chunk
     const FwdArgs& a = sv.jobs[job].fwd;
     const uint64_t chunks = (a.units + a.chunk - 1) / a.chunk;
-    const uint64_t n_items = (chunks + kFwdClaims - 1) / kFwdClaims;
-    for (uint64_t i = 0; i < n_items; ++i) items.push_back({job, K_FWD, gen, 0, 0, 0});
+    const uint64_t claims = std::max<uint64_t>(1, kFwdItemUnits / a.chunk);
+    const uint64_t n_items = (chunks + claims - 1) / claims;
+    for (uint64_t i = 0; i < n_items; ++i) items.push_back({job, K_FWD, gen, 0, claims, 0});
   } else if (phase == PH_REDUCE) {
     for (uint64_t b = 0; b < g.S; b += kReduceChunk)
       items.push_back({job, K_REDUCE, gen, b, std::min<uint64_t>(g.S, b + kReduceChunk), 0});
