@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(1024, 1)
   sm.stage = reinterpret_cast<PointPair*>(smem + hist_bytes);
   sm.bars = reinterpret_cast<uint64_t*>(sm.stage + (size_t)a.stages * a.ppb);
   sm.units = reinterpret_cast<unsigned long long*>(sm.bars + 2 * a.stages);
+  sm.rows = reinterpret_cast<uint32_t*>(sm.units + a.stages + 1);
   if (threadIdx.x == 0) {
     for (uint32_t i = 0; i < a.stages; ++i) {
       mbar_init(&sm.bars[i], 1);                                 // full
@@ -213,7 +214,8 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
     a.stages = 2;
   }
   // staged blocks, then full + empty barriers and the unit number of each slot
-  const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 24 * a.stages + 64;
+  const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 24 * a.stages + 64 +
+                             4 * kRowWords;
   size_t smem;
   if (moments) {
     // window rows plus 2J halo rows fit the kMomRows moment histograms

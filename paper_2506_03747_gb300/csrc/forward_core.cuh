@@ -298,7 +298,11 @@ struct FwdSmem {
   PointPair* stage;            // [stages][ppb]
   uint64_t* bars;              // full[stages] then empty[stages] (initialised by the caller)
   unsigned long long* units;   // [stages]: the unit staged in each slot
+  uint32_t* rows = nullptr;    // [kRowWords] or null: row tracking (see fwd_run_ws)
 };
+// rows: 32 words for the producer's lanes, then one per slot (up to 8 stages)
+constexpr int kMaxRangedStages = 8;
+constexpr int kRowWords = 32 + kMaxRangedStages;
 
 constexpr unsigned long long kNoUnit = ~0ull;  // end of a run (in FwdSmem::units)
 
@@ -867,10 +871,10 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
   __shared__ int s_abort;
   __shared__ uint32_t s_used;  // slots this call used (units + the end mark)
   // rows each lane's unit can touch (producer), and for each slot the rows
-  // its tile's units so far can touch (consumers)
-  constexpr int kMaxRangedStages = 8;
-  __shared__ uint32_t s_lane_rows[32];
-  __shared__ uint32_t s_slot_rows[kMaxRangedStages];
+  // its tile's units so far can touch (consumers), in the caller's shared
+  // memory (static arrays here would be repeated in every instantiation)
+  uint32_t* const s_lane_rows = sm.rows;
+  uint32_t* const s_slot_rows = sm.rows + 32;
   float* hist = sm.hist;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -887,7 +891,8 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
   const bool cull = NLOS_FWD_CULL && a.bounds != nullptr && MODE != MODE_NEAREST_COUNT;
   // histogram rows tracked per tile (flush and zero only those); the moment
   // histograms have their own layout and are always handled whole
-  const bool ranged = RANGED && cull && MODE != MODE_SPLAT_MOM && stages <= kMaxRangedStages;
+  const bool ranged = RANGED && sm.rows != nullptr && cull && MODE != MODE_SPLAT_MOM &&
+                      stages <= kMaxRangedStages;
   if (warp == 0) {
     // The whole warp walks the units 32 at a time: each lane tests one unit
     // against the bounds (unit_live), then lane 0 stages the live ones in

@@ -186,8 +186,8 @@ template <int SCAN, int COS, int MODE>
 __device__ NLOS_SERVE_FWD_INLINE bool fwd_item_mode(const FwdArgs& a, const FwdSmem& sm,
                                                     uint32_t& it, uint32_t claims) {
   FwdCount cnt;
-  // whole-window flushes: the row tracking's static shared memory would not
-  // fit beside this kernel's dynamic shared memory
+  // whole-window flushes: row tracking costs this kernel spills, which made
+  // large requests' forward items slower than the flush work it saves
   const bool ok = fwd_run_ws<SCAN, COS, MODE, 4, false>(a, 0, 0, sm, kServeStages, cnt, nullptr,
                                                      it, a.next_chunk, a.chunk, a.units,
                                                      claims);
