@@ -1,9 +1,10 @@
 """Serving through the C ABI: each request served in a mix of concurrent
 requests equals the same request simulated alone (per-bin tolerance on the
 noise-free transient; Poisson counts equal except where lambda differs in its
-last bits), admission respects the HBM budget, and host-injected faults
-(cancellation, refused allocation, a withheld work-item publication that the
-device's bounded wait turns into NLOS_ETIMEOUT) leave the server usable."""
+last bits), admission respects the HBM budget, a small request does not wait
+for a large one submitted before it, and host-injected faults (cancellation,
+refused allocation, a withheld work-item publication that the device's
+bounded wait turns into NLOS_ETIMEOUT) leave the server usable."""
 import time
 
 import numpy as np
@@ -188,4 +189,45 @@ def test_withheld_publication_times_out_and_server_recovers():
     a_tau, _, _ = _alone(prm, pts)
     H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=H.REL_BIN, what="after fault")
     srv.release(t2)
+    srv.destroy()
+
+
+def test_small_request_is_not_queued_behind_a_large_one():
+    """Publication order: a small request submitted just after a large one
+    finishes first (its short phases take the express ring, its forward items
+    go ahead of the large request's unpublished ones), and both results match
+    the request simulated alone."""
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(scenes.SEED_BASE + 2)
+    big_pts, _ = scenes.primitive_union_points(rng, 1 << 20)
+    big = scenes.default_params(scan_nx=128, scan_ny=128, wall_half_x=1.0, wall_half_y=1.0,
+                                bin_width_s=8e-12, num_bins=1024, standoff_m=1.0,
+                                standoff_mode="euclidean", window_start_m=2.6,
+                                jitter_fwhm_s=60e-12, noise_mode="none")
+    small_pts = big_pts[:2000].copy()
+    small = dict(big, scan_nx=16, scan_ny=16, num_bins=512)
+    srv = nlos.server_create(16 << 30)
+    done = {}
+    t_big = srv.submit(big, big_pts)
+    time.sleep(0.002)
+    t_small = srv.submit(small, small_pts)
+    pending = {"big": t_big, "small": t_small}
+    deadline = time.time() + 60.0
+    while pending and time.time() < deadline:
+        for name, t in list(pending.items()):
+            st, _, _, _ = srv.poll(t, wait_ms=0)
+            if st == nlos.OK:
+                done[name] = time.perf_counter()
+                del pending[name]
+        time.sleep(0.0002)
+    assert not pending, "requests did not finish"
+    assert done["small"] < done["big"], "the small request waited for the large one"
+    st, tau_ptr, _, _ = srv.poll(t_small, wait_ms=0)
+    got = _fetch(tau_ptr, (256, 512), torch.float32).astype(np.float64)
+    a_tau, _, _ = _alone(small, small_pts)
+    H.check_bins(got, a_tau.astype(np.float64), rel=1e-4,
+                 what="small request served behind a large one")
+    srv.release(t_small)
+    srv.release(t_big)
     srv.destroy()
