@@ -226,3 +226,24 @@ def test_union_self_occlusion_sampled(cos_mode):
         err = np.abs(got[s] - want)
         assert np.all(err <= allow + 1e-12 * np.abs(want).max() + 1e-300), s
     assert n_hidden > 0  # the scene does shadow itself
+
+
+def test_threshold_one_hides_nothing_and_more_occluders_only_remove_light():
+    """Invariants: a chord never exceeds the whole segment, so with eta = 1 no
+    pair is hidden (the plain forward, bit for bit); and every pair hidden by a
+    set of occluders stays hidden when occluders are added, so each bin can only
+    lose weight."""
+    rng = np.random.default_rng(scenes.SEED_BASE + 2)
+    pts, prims = scenes.primitive_union_points(rng, 600)
+    occ = scenes.occluder_records(prims)
+    params = scenes.default_params(scan_nx=4, scan_ny=3, wall_half_x=1.0, wall_half_y=1.0,
+                                   bin_width_s=16e-12, num_bins=1024, standoff_m=0.0,
+                                   standoff_mode="constant", cos_mode="none")
+    plain = oracle.forward_binned(params, pts)["tau"]
+    assert np.array_equal(oracle.forward_binned(params, pts, occ=occ, eta=1.0)["tau"], plain)
+    prev = plain
+    for k in range(1, len(occ) + 1):
+        cur = oracle.forward_binned(params, pts, occ=occ[:k])["tau"]
+        assert np.all(cur <= prev + 1e-12 * plain.max())
+        prev = cur
+    assert prev.sum() < plain.sum()
