@@ -562,7 +562,11 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
     th.start()
     pending = set(range(len(reqs)))
     deadline = time.perf_counter() + 120.0 + reqs[-1]["arrival_s"]
+    peak_resident, t_res = 0, 0.0
     while pending:
+        if time.perf_counter() - t_res > 0.005:  # sampled, not on every poll: it takes the server lock
+            peak_resident = max(peak_resident, srv.stats()["resident_bytes"])
+            t_res = time.perf_counter()
         if time.perf_counter() > deadline:  # bounded: report what did not finish
             failures.append((sorted(pending)[:5], "not finished within the replay deadline"))
             for i in pending:
@@ -626,7 +630,8 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
     return {"requests": len(reqs), "arrival_rate_hz": rate_hz, "budget_gb": budget_gb,
             "offered_pairs_per_s": tot_pairs / reqs[-1]["arrival_s"],
             "continuous_batching": dict(summ(lat_b, span_b), device_cycle_shares={
-                k: v / max(1, sum(cyc.values())) for k, v in cyc.items()}),
+                k: v / max(1, sum(cyc.values())) for k, v in cyc.items()},
+                peak_resident_bytes=int(peak_resident)),
             "one_at_a_time": summ(lat_1, span_1),
             "failures": failures[:5]}
 
