@@ -178,7 +178,9 @@ nlos_status nlos_scene_set_points(nlos_scene* scene, const float* points_aos8, u
  * FP32 rounding. Non-confocal scans test the laser leg once per point when
  * the points are packed (FP64); the detector leg is tested per pair (FP32).
  * occluders: host memory, copied; count 0 removes them. The points are
- * re-packed on cuda_stream (asynchronous). NLOS_EINVAL: count above
+ * re-packed on cuda_stream (asynchronous; like every call on a scene, it must
+ * not overlap on the device with other work on the same scene), and later
+ * forwards use the new set. Serving requests carry no occluders. NLOS_EINVAL: count above
  * NLOS_MAX_OCCLUDERS, an unknown kind, a non-finite value, a radius <= 0 or
  * a box with a >= b on some axis. While a scene has occluders, nlos_forward
  * and nlos_simulate need bin_mode = NLOS_BIN_NEAREST and boundary_eps = 0
