@@ -69,6 +69,8 @@ def test_host_side_argument_checks_without_gpu(lib):
     p.bin_mode = nlos.BIN_SPLAT  # splat without jitter width
     assert lib.nlos_scene_create(ctypes.byref(p), None, 0, 0, None, ctypes.byref(h)) == nlos.EINVAL
     assert lib.nlos_simulate(None, None, None, None, None, None) == nlos.EINVAL
+    assert lib.nlos_scene_set_occluders(None, None, 0, None) == nlos.EINVAL
+    assert b"scene is NULL" in nlos.load().nlos_last_error()
     assert lib.nlos_abi_version() == 1
 
 
