@@ -3,10 +3,12 @@
 
 Metric: pair-interactions/s of the whole forward hot path (ingest/pack,
 pair histogram with fused jitter, FP64 energy reduction, Philox Poisson
-noise) on the 64x64-scan union-of-primitives workload (confocal, 2 m x 2 m,
-512 bins of 8 ps, 1 m stand-off, 262,144 surface points, 60 ps jitter,
-100-photon peak + 1e-3 dark counts), with inputs resident in HBM. One JSON
-line on rank 0; see --help.
+noise), inputs resident in HBM, on the largest single-GPU workload: the
+non-confocal 128x128-scan heightfield (1,048,576 surface points, 1024 bins of
+4 ps, 1.5 m stand-off, 30 ps jitter, 100-photon peak + 1e-3 dark counts;
+1.72e10 pairs per pass). The confocal union-of-primitives workload (64x64
+scan, 262,144 points, 512 bins of 8 ps) is reported beside it under
+"union64". One JSON line on rank 0; see --help.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -33,11 +35,22 @@ METRIC = "pair-interactions/s vs FP32 roofline; served p50/p99 latency vs one-by
 UNIT = "pairs/s"
 FP32_SLOTS_PER_PAIR = 17   # algorithmic FP32 issue slots per evaluated pair
 FP32_SLOTS_EARLY_OUT = 6   # slots of a pair stopped by the early out (dx, dy, r^2, cosine)
+MUFU_PER_PAIR = 2          # square root and reciprocal estimates per evaluated pair
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-WORKLOAD_DESC = ("union64: confocal 64x64 scan over 2 m x 2 m, 512 bins x 8 ps, stand-off 1 m "
-                 "(Euclidean legs), 262,144 area-uniform points on a seeded union of 3-6 "
-                 "spheres/boxes at 0.3-1.2 m, albedo U[0.2,1], jitter FWHM 60 ps, Poisson noise "
-                 "peak 100 photons + 1e-3 dark/bin")
+HEADLINE = "heightfield128"
+WORKLOAD_DESC = {
+    "heightfield128": (
+        "heightfield128: non-confocal (laser at the wall centre) 128x128 detector scan over "
+        "2 m x 2 m, 1024 bins x 4 ps, stand-off 1.5 m (Euclidean legs), acquisition window from "
+        "L0 = 3.8 m (2 x 1.5 m + 2 x 0.4 m: the earliest round trip from the wall centre), "
+        "1,048,576 points of a seeded 1024x1024 heightfield at 0.4-1.5 m, albedo Beta(2,2), "
+        "jitter FWHM 30 ps, Poisson noise peak 100 photons + 1e-3 dark/bin"),
+    "union64": (
+        "union64: confocal 64x64 scan over 2 m x 2 m, 512 bins x 8 ps, stand-off 1 m "
+        "(Euclidean legs), acquisition window from L0 = 2.6 m (2 x 1 m + 2 x 0.3 m), "
+        "262,144 area-uniform points on a seeded union of 3-6 spheres/boxes at 0.3-1.2 m, "
+        "albedo U[0.2,1], jitter FWHM 60 ps, Poisson noise peak 100 photons + 1e-3 dark/bin"),
+}
 
 
 def _dist():
@@ -62,16 +75,16 @@ def whole_job_rate(units_per_rank: float, seconds: float, world_size: int, dist=
     return world_size * units_per_rank / t, t
 
 
-def workload_seed(rank: int) -> int:
+def workload_seed(name: str, rank: int) -> int:
     """Each rank simulates its own independent scene of the same workload."""
     import scenes
-    return scenes.SEED_BASE + 2 + 1000 * rank
+    return scenes.SEED_BASE + (3 if name == "heightfield128" else 2) + 1000 * rank
 
 
-def _workload(rank: int):
+def _workload(name: str, rank: int):
     import scenes
-    params, pts = scenes.workload_union64(seed=workload_seed(rank))
-    return params, pts
+    fn = scenes.workload_heightfield128 if name == "heightfield128" else scenes.workload_union64
+    return fn(seed=workload_seed(name, rank))
 
 
 class ClockSampler:
@@ -141,10 +154,10 @@ def forward_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def _traffic_for():
-    """DRAM bytes per forward launch from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "forward_union64_traffic.json")
+def _traffic_for(name: str):
+    """DRAM bytes per forward launch from the committed ncu summary of this
+    workload, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"forward_{name}_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -153,51 +166,203 @@ def _traffic_for():
     return d.get("dram_bytes_per_launch") if ok else None
 
 
+def _sample_range(S: int, count: int) -> tuple:
+    """A contiguous block of scan points around the middle of the scan (the
+    oracle's cost per pair does not depend on which)."""
+    count = max(1, min(S, count))
+    begin = max(0, S // 2 - count // 2)
+    return begin, count
+
+
 def cpu_baseline(params, pts, scan_count: int):
-    """The FP64 oracle as it stands, on all host cores, on the first scan_count
-    scan points of the workload (forward + jitter + energy + noise)."""
+    """The FP64 oracle as it stands, on all host cores, on a block of
+    scan_count scan points of the workload (forward + jitter + energy +
+    noise); pairs/s of that sample."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
+    S = params["scan_nx"] * params["scan_ny"]
+    s0, n = _sample_range(S, scan_count)
     t0 = time.perf_counter()
-    oracle.simulate(params, pts, 0, scan_count, threads=cores)
+    oracle.simulate(params, pts, s0, n, threads=cores)
     dt = time.perf_counter() - t0
-    pairs = scan_count * pts.shape[0]
+    pairs = n * pts.shape[0]
     return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"scan points 0..{scan_count - 1} of {params['scan_nx'] * params['scan_ny']}"
-                      f" x all {pts.shape[0]} points, one pass (FP64 forward + jitter + energy + "
-                      f"Poisson noise), {dt:.2f} s wall"}
+            "sample": f"scan points {s0}..{s0 + n - 1} of {S} x all {pts.shape[0]} points, one "
+                      f"pass (FP64 forward + jitter + energy + Poisson noise), {dt:.2f} s wall"}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    params, pts = _workload(0)
+    params, pts = _workload(HEADLINE, 0)
     S = params["scan_nx"] * params["scan_ny"]
-    scan_count = 512  # bounded sample per step (1/8 of the scan)
+    s0, n = _sample_range(S, args.ref_scan)  # bounded sample per step
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.simulate(params, pts, 0, scan_count, threads=cores)
+        oracle.simulate(params, pts, s0, n, threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.simulate(params, pts, 0, scan_count, threads=cores)
+        oracle.simulate(params, pts, s0, n, threads=cores)
     dt = time.perf_counter() - t0
-    pairs = args.steps * scan_count * pts.shape[0]
+    pairs = args.steps * n * pts.shape[0]
     v = pairs / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_DESC,
-                                            "sample_per_step": f"{scan_count} of {S} scan points"},
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC[HEADLINE],
+                                            "sample_per_step": f"{n} of {S} scan points"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{scan_count} of {S} scan points x {pts.shape[0]} points "
-                                       "per step"},
+                             "sample": f"scan points {s0}..{s0 + n - 1} of {S} x "
+                                       f"{pts.shape[0]} points per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def device_peaks():
+    """Measured element rates per SM clock (nlos_measure_peaks), or None."""
+    from paper_2506_03747_gb300 import nlos
+    try:
+        return nlos.measure_peaks()
+    except Exception:  # measurement only; the roofline then says so
+        return None
+
+
+def forward_roofline(name, fwd_s, st, pairs_per_step, n_sm, sm_max_mhz, peaks, S, B):
+    """Roofline of the pair-histogram kernel: evaluated pairs (full-evaluation
+    equivalents) per second against the binding one of the FP32 pipe (17
+    slots per pair) and the MUFU pipe (2 estimates per pair) at the measured
+    per-SM rates and the maximum SM clock."""
+    f = sm_max_mhz * 1e6
+    if peaks:
+        ffma, mufu, basis = peaks["ffma"], peaks["sqrt_approx"], "measured (nlos_measure_peaks)"
+    else:
+        ffma, mufu, basis = 128.0, 16.0, "nominal (128 FP32 lanes, 16 MUFU lanes per SM clock)"
+    fp32_peak = n_sm * ffma * f / FP32_SLOTS_PER_PAIR
+    mufu_peak = n_sm * mufu * f / MUFU_PER_PAIR
+    peak = min(fp32_peak, mufu_peak)
+    full, tested = int(st["pairs_full"]), int(st["pairs_tested"])
+    # pairs of culled units cost nothing per pair and are not counted as work
+    work = full + max(0, tested - full) * FP32_SLOTS_EARLY_OUT / FP32_SLOTS_PER_PAIR
+    achieved = work / fwd_s
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": _traffic_for(name),
+            "kernel": "fwd_kernel (pair histogram + fused jitter)",
+            "peak_basis": f"min(FP32: {n_sm} SMs x {ffma:.1f} FMA lanes/clk x {sm_max_mhz:.0f} MHz / "
+                          f"{FP32_SLOTS_PER_PAIR} slots per pair = {fp32_peak / 1e9:.0f} Gpair/s; "
+                          f"MUFU: {n_sm} x {mufu:.1f} lanes/clk x {sm_max_mhz:.0f} MHz / "
+                          f"{MUFU_PER_PAIR} per pair = {mufu_peak / 1e9:.0f} Gpair/s), {basis}",
+            "work_basis": f"full-evaluation-equivalent pairs: pairs evaluated in full + "
+                          f"{FP32_SLOTS_EARLY_OUT}/{FP32_SLOTS_PER_PAIR} x pairs stopped by "
+                          f"the early out; pairs of units ruled out by the block bounds "
+                          f"count 0",
+            "pairs_full_fraction": full / pairs_per_step,
+            "pairs_tested_fraction": tested / pairs_per_step,
+            "effective_pairs_per_s": pairs_per_step / fwd_s,
+            "kernel_ms": fwd_s * 1e3,
+            "tau_write_gbs": S * B * 4 / fwd_s / 1e9}
+
+
+def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=None):
+    """Times `steps` bench steps of one workload (scene_set_points = ingest and
+    pack, forward = pair histogram with fused jitter, detect = FP64 energy,
+    cube statistics and Poisson noise), inputs resident in HBM, L2 flushed
+    between steps; then the same steps end to end with host buffers."""
+    import torch
+    from paper_2506_03747_gb300 import nlos
+    params, pts_np = _workload(name, rank)
+    stream = torch.cuda.current_stream()
+    pts_dev = torch.from_numpy(pts_np).cuda()
+    scene = nlos.scene_create(nlos.params(params), pts_dev)
+    S, B, P = scene.num_scan, scene.num_bins, scene.num_points
+    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    counts = torch.empty((S, B), dtype=torch.int32, device="cuda")
+    energy = torch.empty(S, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    pairs_per_step = S * P
+
+    def step():
+        nlos.scene_set_points(scene, pts_dev)
+        nlos.forward(scene, tau)
+        nlos.detect(scene, tau, counts, energy)
+
+    for _ in range(max(3, warmup)):
+        step()
+    nlos.scene_check(scene)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()  # evict L2 between timed steps (outside the step events)
+        e = ev[k]
+        e[0].record(stream)
+        nlos.scene_set_points(scene, pts_dev)
+        e[1].record(stream)
+        nlos.forward(scene, tau)
+        e[2].record(stream)
+        nlos.detect(scene, tau, counts, energy)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if clocks else None
+    nlos.scene_check(scene)
+    step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
+    pack_ms = np.array([e[0].elapsed_time(e[1]) for e in ev])
+    fwd_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
+    det_ms = np.array([e[2].elapsed_time(e[3]) for e in ev])
+    value, t_total = whole_job_rate(steps * pairs_per_step, float(step_ms.sum()) * 1e-3, ws,
+                                    dist, "cuda")
+
+    # ---- end to end through the C ABI with host buffers (pinned) ----------
+    pts_host = torch.from_numpy(pts_np).pin_memory()
+    counts_host = torch.empty((S, B), dtype=torch.int32).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+    for _ in range(2):
+        nlos.scene_set_points(scene, pts_host)
+        nlos.forward(scene, tau)
+        nlos.detect(scene, tau, counts, energy)
+        counts_host.copy_(counts, non_blocking=True)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        a, b = e2e_ev[k]
+        a.record(stream)
+        nlos.scene_set_points(scene, pts_host)          # H2D of the step's points
+        nlos.forward(scene, tau)
+        nlos.detect(scene, tau, counts, energy)
+        counts_host.copy_(counts, non_blocking=True)    # D2H of the step's result
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_rate, _ = whole_job_rate(steps * pairs_per_step,
+                                 sum(a.elapsed_time(b) for a, b in e2e_ev) * 1e-3, ws, dist, "cuda")
+    e2e = {"value": e2e_rate, "unit": UNIT,
+           "h2d_bytes_per_step": int(pts_np.nbytes), "d2h_bytes_per_step": int(S * B * 4)}
+
+    props = torch.cuda.get_device_properties(local)
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+    st = nlos.simulate(scene, tau, counts, energy, stats=True)
+    roof = forward_roofline(name, float(fwd_ms.mean()) * 1e-3, st, pairs_per_step,
+                            props.multi_processor_count, sm_max, peaks, S, B)
+    scene.destroy()
+    return {"value": value, "ms_per_step": t_total * 1e3 / steps,
+            "transients_per_s": ws * steps * S / t_total, "wall_s": wall, "clocks": clk,
+            "phase_ms": {"ingest_pack": float(pack_ms.mean()), "forward": float(fwd_ms.mean()),
+                         "detect": float(det_ms.mean())},
+            "roofline": roof, "e2e": e2e, "params": params, "pts": pts_np,
+            "shape": {"scan_points": S, "bins": B, "points": P, "pairs_per_step": pairs_per_step}}
 
 
 def run_ours(args):
@@ -212,130 +377,39 @@ def run_ours(args):
     from paper_2506_03747_gb300 import nlos
     nbuild.build()
     nlos.load()
+    peaks = device_peaks()
 
-    params, pts_np = _workload(rank)
-    prm = nlos.params(params)
-    stream = torch.cuda.current_stream()
-    pts_dev = torch.from_numpy(pts_np).cuda()
-    scene = nlos.scene_create(prm, pts_dev)
-    S, B, P = scene.num_scan, scene.num_bins, scene.num_points
-    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
-    counts = torch.empty((S, B), dtype=torch.int32, device="cuda")
-    energy = torch.empty(S, dtype=torch.float64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    pairs_per_step = S * P
-
-    def step():
-        nlos.scene_set_points(scene, pts_dev)
-        nlos.forward(scene, tau)
-        nlos.detect(scene, tau, counts, energy)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    nlos.scene_check(scene)
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()  # evict L2 between timed steps (outside the step events)
-        e = ev[k]
-        e[0].record(stream)
-        nlos.scene_set_points(scene, pts_dev)
-        e[1].record(stream)
-        nlos.forward(scene, tau)
-        e[2].record(stream)
-        nlos.detect(scene, tau, counts, energy)
-        e[3].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    nlos.scene_check(scene)
-    step_ms = np.array([e[0].elapsed_time(e[3]) for e in ev])
-    fwd_ms = np.array([e[1].elapsed_time(e[2]) for e in ev])
-    value, t_total = whole_job_rate(args.steps * pairs_per_step, float(step_ms.sum()) * 1e-3, ws,
-                                    dist, "cuda")
-
-    # ---- end to end through the C ABI with host buffers (pinned) ----------
-    pts_host = torch.from_numpy(pts_np).pin_memory()
-    counts_host = torch.empty((S, B), dtype=torch.int32).pin_memory()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-    for _ in range(2):
-        nlos.scene_set_points(scene, pts_host)
-        nlos.forward(scene, tau)
-        nlos.detect(scene, tau, counts, energy)
-        counts_host.copy_(counts, non_blocking=True)
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        a, b = e2e_ev[k]
-        a.record(stream)
-        nlos.scene_set_points(scene, pts_host)          # H2D of the step's points
-        nlos.forward(scene, tau)
-        nlos.detect(scene, tau, counts, energy)
-        counts_host.copy_(counts, non_blocking=True)    # D2H of the step's result
-        b.record(stream)
-    torch.cuda.synchronize()
-    e2e_rate, _ = whole_job_rate(args.steps * pairs_per_step,
-                                 sum(a.elapsed_time(b) for a, b in e2e_ev) * 1e-3, ws, dist, "cuda")
-    e2e = {"value": e2e_rate, "unit": UNIT,
-           "h2d_bytes_per_step": int(pts_np.nbytes), "d2h_bytes_per_step": int(S * B * 4)}
-
-    # ---- roofline of the dominant kernel (the pair histogram) -------------
-    props = torch.cuda.get_device_properties(local)
-    n_sm = props.multi_processor_count
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    peak_pairs = n_sm * 128 * sm_max * 1e6 / FP32_SLOTS_PER_PAIR
-    fwd_mean = float(fwd_ms.mean()) * 1e-3
-    # pairs that went through the full evaluation; the others stopped after
-    # r^2 and the cosine numerator (the warp-uniform early out)
-    st = nlos.simulate(scene, tau, counts, energy, stats=True)
-    full = int(st["pairs_full"])
-    tested = int(st["pairs_tested"])
-    # pairs of culled units cost nothing per pair and are not counted as work
-    work = full + max(0, tested - full) * FP32_SLOTS_EARLY_OUT / FP32_SLOTS_PER_PAIR
-    achieved = work / fwd_mean
-    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_pairs / 1e9,
-            "unit": "Gpair/s", "frac": achieved / peak_pairs,
-            "traffic": _traffic_for(),
-            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / "
-                          f"{FP32_SLOTS_PER_PAIR} FP32 slots per pair",
-            "work_basis": f"full-evaluation-equivalent pairs: pairs evaluated in full + "
-                          f"{FP32_SLOTS_EARLY_OUT}/{FP32_SLOTS_PER_PAIR} x pairs stopped by "
-                          f"the early out; pairs of units ruled out by the block bounds "
-                          f"count 0",
-            "pairs_full_fraction": full / pairs_per_step,
-            "pairs_tested_fraction": tested / pairs_per_step,
-            "effective_pairs_per_s": pairs_per_step / fwd_mean,
-            "kernel_ms": fwd_mean * 1e3}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps,
+    head = measure_workload(HEADLINE, rank, args.steps, args.warmup, local, dist, ws, peaks,
+                            clocks=ClockSampler(local))
+    extra = None
+    if args.union_steps > 0:
+        extra = measure_workload("union64", rank, args.union_steps, args.warmup, local, dist, ws,
+                                 peaks)
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "scan_points": S, "bins": B, "points": P,
-                       "pairs_per_step": pairs_per_step,
-                       "l2": "flushed by a 256 MB write between timed steps (outside the step "
-                             "events)",
-                       "step": "scene_set_points (pack) + forward (pair histogram + fused "
-                               "jitter) + detect (FP64 energy/peak + Poisson noise)",
-                       "parallelism": f"{ws} independent scenes, one per GPU"},
-            "transients_per_s": ws * args.steps * S / t_total,
-            "wall_s": wall, "clocks": clk, "gpu_launches": 4 * args.steps,
-            "roofline": roof, "e2e": e2e}
+            "config": dict({"workload": WORKLOAD_DESC[HEADLINE]}, **head["shape"],
+                           l2="flushed by a 256 MB write between timed steps (outside the step "
+                              "events)",
+                           step="scene_set_points (ingest: spatial order + pack + bounds) + "
+                                "forward (pair histogram + fused jitter) + detect (FP64 energy, "
+                                "cube max and sums, Poisson noise)",
+                           parallelism=f"{ws} independent scenes, one per GPU"),
+            "transients_per_s": head["transients_per_s"], "wall_s": head["wall_s"],
+            "clocks": head["clocks"], "gpu_launches": 8 * args.steps,
+            "phase_ms": head["phase_ms"], "roofline": head["roofline"], "e2e": head["e2e"]}
+    if peaks:
+        line["device_peaks_per_sm_clock"] = peaks
+    if extra is not None:
+        line["union64"] = {"workload": WORKLOAD_DESC["union64"], **extra["shape"],
+                           "value": extra["value"], "ms_per_step": extra["ms_per_step"],
+                           "phase_ms": extra["phase_ms"], "roofline": extra["roofline"],
+                           "e2e": extra["e2e"]}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(params, pts_np, args.cpu_scan)
+        line["cpu_baseline"] = cpu_baseline(head["params"], head["pts"], args.cpu_scan)
     if rank == 0 and ws == 1 and args.splat_steps > 0:
-        line["splat_adjoint"] = splat_adjoint_bench(args.splat_steps, 1)
+        line["splat_adjoint"] = splat_adjoint_bench(args.splat_steps, 1, peaks)
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         line["serving"] = serving_bench(args.serving_requests, args.serving_rate)
     if rank == 0 and ws == 1 and args.lct_steps > 0:
@@ -344,7 +418,6 @@ def run_ours(args):
         line["occlusion"] = occlusion_bench(args.occlusion_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    scene.destroy()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -451,7 +524,43 @@ def lct_bench(steps: int):
             "shape_correlation_lct_vs_direct": corr}
 
 
-def splat_adjoint_bench(steps: int, warmup: int):
+def splat_moment_reds(params, pts, n_sample=128, seed=7):
+    """Shared reductions per pass of the moment-form splat forward, counted on
+    the host on a sample of scan points and scaled to the scan: six per
+    (pair, bin window) whose moment row floor(u) - w0 + J lies inside the
+    window's bw + 2J rows, for facing pairs of nonzero weight (the kernel's
+    predicate). Windows as the launch chooses them: J = ceil(6 sigma) + 1,
+    at most 256 - 2J bins each, rounded up to multiples of 4."""
+    import math
+    C = 299792458.0
+    sig = params["jitter_fwhm_s"] / (2.0 * math.sqrt(2.0 * math.log(2.0)) * params["bin_width_s"])
+    J = math.ceil(6.0 * sig) + 1
+    B = params["num_bins"]
+    max_bw = (256 - 2 * J) & ~3
+    n_win = -(-B // max_bw)
+    bw = ((-(-B // n_win)) + 3) & ~3
+    nx, ny, w = params["scan_nx"], params["scan_ny"], params["wall_half_x"]
+    rng = np.random.default_rng(seed)
+    S = nx * ny
+    ids = rng.choice(S, size=min(S, n_sample), replace=False)
+    sx = -w + (ids % nx + 0.5) * (2 * w / nx)
+    sy = -params["wall_half_y"] + (ids // nx + 0.5) * (2 * params["wall_half_y"] / ny)
+    p = pts.astype(np.float64)
+    q = p[:, 6] * p[:, 7]
+    dx = sx[:, None] - p[None, :, 0]
+    dy = sy[:, None] - p[None, :, 1]
+    r = np.sqrt(dx * dx + dy * dy + p[None, :, 2] ** 2)
+    cn = p[None, :, 3] * dx + p[None, :, 4] * dy - p[None, :, 5] * p[None, :, 2]
+    j = np.floor(2.0 * r / (C * params["bin_width_s"]))  # no stand-off, L0 = 0
+    ok = (cn > 0) & (q[None, :] > 0)
+    count = 0
+    for k in range(n_win):
+        row = j - k * bw + J
+        count += int(((row >= 0) & (row < bw + 2 * J) & ok).sum())
+    return 6.0 * count * S / len(ids)
+
+
+def splat_adjoint_bench(steps: int, warmup: int, peaks=None):
     """Differentiable path on the 8-scene glyph batch (64x64 scan, 65,536 points
     per scene, 512 bins x 8 ps, splat with 60 ps FWHM): per step, for every
     scene, the splat forward, the L2-loss gradient 2 (tau - target) and the
@@ -507,13 +616,29 @@ def splat_adjoint_bench(steps: int, warmup: int):
     pairs = len(scs) * S * P
     for sc in scs:
         sc.destroy()
-    return {"workload": "8 glyph-plane scenes, 64x64 scan, 65,536 points, 512 bins x 8 ps, "
-                        "splat FWHM 60 ps, L2 loss",
-            "pairs_per_step": pairs, "steps": steps,
-            "ms_per_step": total * 1e3 / steps,
-            "forward_pairs_per_s": steps * pairs / f,
-            "adjoint_pairs_per_s": steps * pairs / b,
-            "train_step_pairs_per_s": steps * pairs / total}
+    out = {"workload": "8 glyph-plane scenes, 64x64 scan, 65,536 points, 512 bins x 8 ps, "
+                       "splat FWHM 60 ps, L2 loss",
+           "pairs_per_step": pairs, "steps": steps,
+           "ms_per_step": total * 1e3 / steps,
+           "forward_pairs_per_s": steps * pairs / f,
+           "adjoint_pairs_per_s": steps * pairs / b,
+           "train_step_pairs_per_s": steps * pairs / total}
+    # shared-atomic roofline of the splat forward (moment form: six shared
+    # f32 reductions per pair and window in range)
+    if peaks:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        f_max = 2070e6
+        reds = sum(splat_moment_reds(params, p) for p in sc_pts)
+        achieved = steps * reds / f
+        peak = props.multi_processor_count * peaks["red_f32"] * f_max
+        out["forward_roofline"] = {
+            "bound": "shared_atomic", "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "unit": "G red.shared.add.f32 lanes/s", "frac": achieved / peak,
+            "peak_basis": f"{props.multi_processor_count} SMs x {peaks['red_f32']:.2f} lanes/clk "
+                          f"(measured, all lanes active) x 2070 MHz",
+            "work_basis": "6 reductions per (pair, bin window) with the moment row in range, "
+                          "counted on the host on 128 sampled scan points per scene"}
+    return out
 
 
 def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
@@ -646,6 +771,11 @@ def main():
                     help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--cpu-scan", type=int, default=2048,
                     help="scan points in the CPU baseline sample")
+    ap.add_argument("--ref-scan", type=int, default=256,
+                    help="scan points per step of the reference (oracle) arm")
+    ap.add_argument("--union-steps", type=int, default=10,
+                    help="timed steps of the union64 workload reported beside the headline "
+                         "(0: skip)")
     ap.add_argument("--splat-steps", type=int, default=2,
                     help="steps of the differentiable-path measurement (0: skip)")
     ap.add_argument("--lct-steps", type=int, default=3,

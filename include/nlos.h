@@ -158,6 +158,21 @@ nlos_status nlos_scene_create(const nlos_params* params, const float* points_aos
                               uint64_t num_points, int points_on_device, void* cuda_stream,
                               nlos_scene** out);
 
+/* A scene for the scan rows [row_begin, row_begin + row_count) of the grid
+ * that params describes (spots, stand-off legs and window as in the whole
+ * grid), for a cube split over devices by scan rows: transients are
+ * independent of one another (the jitter section: each scan position is
+ * recorded on its own), so each device holds all points and simulates its own
+ * rows. Its outputs are [row_count][scan_nx][num_bins]; its Philox streams
+ * are those of the global bin indices (row_begin * scan_nx * num_bins + i),
+ * so the noise does not depend on the split. nlos_detect on such a scene
+ * scales the noise by its own rows; nlos_noise_part scales it by the whole
+ * cube. Otherwise as nlos_scene_create (NLOS_EINVAL for an empty or
+ * out-of-range row range). */
+nlos_status nlos_scene_create_rows(const nlos_params* params, const float* points_aos8,
+                                   uint64_t num_points, int points_on_device, uint32_t row_begin,
+                                   uint32_t row_count, void* cuda_stream, nlos_scene** out);
+
 /* Replaces the points of a scene by num_points new records (same count as at
  * creation), re-running the ingest/pack step on cuda_stream. Asynchronous:
  * invalid points are reported by the next nlos_simulate with stats
@@ -165,6 +180,21 @@ nlos_status nlos_scene_create(const nlos_params* params, const float* points_aos
  * (pinned memory keeps the copy asynchronous) when points_on_device == 0. */
 nlos_status nlos_scene_set_points(nlos_scene* scene, const float* points_aos8, uint64_t num_points,
                                   int points_on_device, void* cuda_stream);
+
+/* The differentiable parameterisation of the scene (the adjoint's variables,
+ * nlos_simulate_backward): point p becomes the record last given to
+ * nlos_scene_create / nlos_scene_set_points with its position moved by
+ * depth_dev[p] metres along its own unit normal (x + delta n; normal and patch
+ * area unchanged) and its albedo replaced by albedo_dev[p]; then the scene is
+ * re-ordered and re-packed on the device. albedo_dev, depth_dev: [num_points]
+ * float32 device arrays, each nullable (NULL keeps the given albedo / moves
+ * nothing). The paper has no such parameterisation (it differentiates
+ * nothing); every call starts again from the given records, so calls do not
+ * accumulate. Asynchronous; invalid results (albedo < 0, z <= 0) are reported
+ * like invalid points (nlos_scene_check, nlos_stats.device_error). The first
+ * call allocates a copy of the given records (32 bytes per point). */
+nlos_status nlos_scene_set_albedo_depth(nlos_scene* scene, const float* albedo_dev,
+                                        const float* depth_dev, void* cuda_stream);
 
 /* Occluders: an extension; the paper's model (Eq. 1) has no visibility term,
  * its depth maps keeping only the first surface seen from the wall. A scene
@@ -224,6 +254,17 @@ nlos_status nlos_forward(nlos_scene* scene, float* tau_dev, void* cuda_stream);
 nlos_status nlos_detect(nlos_scene* scene, const float* tau_dev, uint32_t* counts_dev,
                         double* energy_dev, void* cuda_stream);
 
+/* The noise step (Eq. 18/19, Algorithm 1 step 2.4) of a part of a larger cube
+ * (nlos_scene_create_rows): counts_dev [S][B] uint32 ~ Poisson(scale * tau +
+ * dark_per_bin) with the scale of the whole cube, computed on the device from
+ * cube_stats_dev = {max, sum, sum of squares} of the whole cube's jittered
+ * transient (double[3], device: the maximum of the parts' maxima and the sums
+ * of their sums, e.g. nlos_reduce's stats combined across devices) and
+ * cube_bins, the whole cube's bin count (population variance for PAPER_NR).
+ * Asynchronous; NLOS_EINVAL when noise_mode is NONE. */
+nlos_status nlos_noise_part(nlos_scene* scene, const float* tau_dev, uint32_t* counts_dev,
+                            const double* cube_stats_dev, uint64_t cube_bins, void* cuda_stream);
+
 /* Adjoint of the SPLAT forward (bin_mode must be SPLAT): given grad_tau_dev
  * = dL/dtau ([S][B] float32 device), writes dL/d albedo_p and dL/d delta_p
  * ([P] float32 device each, nullable), where delta_p displaces point p along
@@ -274,8 +315,12 @@ nlos_status nlos_reduce_static(const float* tau_dev, uint64_t num_traces, uint32
 /* Poisson noise: counts[i] ~ Poisson(fmaf(scale, tau[i], dark)) drawn from
  * the Philox4x32-10 stream of global bin index index_base + i: key =
  * (seed_lo, seed_hi), counter = (index_lo, index_hi, block, stream_tag),
- * uniforms ((word >> 9) + 0.5) * 2^-23; Knuth's multiplication method for
- * lambda < 30 (single precision), Hoermann's PTRS (1993) otherwise (double). */
+ * uniforms ((word >> 9) + 0.5) * 2^-23. Three exact samplers by range:
+ * lambda < 30, Knuth's multiplication method (single-precision products
+ * against expf(-lambda)); 30 <= lambda < 150, the sum of ceil(lambda / 30)
+ * Knuth draws of mean lambda / ceil(lambda / 30), one after the other from the
+ * same stream (a sum of independent Poisson variables is Poisson);
+ * lambda >= 150, Hoermann's PTRS (1993) in double precision. */
 nlos_status nlos_noise(const float* tau_dev, uint64_t n, float scale, float dark, uint64_t seed,
                        uint32_t stream_tag, uint64_t index_base, uint32_t* counts_dev,
                        void* cuda_stream);
@@ -366,6 +411,34 @@ nlos_status nlos_server_device_cycles(nlos_server* server, uint64_t cycles_out[3
  * request fails with NLOS_ETIMEOUT, while the server keeps running);
  * 2 = refuse its device allocation (the request fails with NLOS_ENOMEM). */
 nlos_status nlos_server_inject(nlos_server* server, int fault);
+
+/* ---- Measurement: throughput of the units the forward is bound by -------- */
+
+/* Element operations per SM clock per SM (clock64 around each timed loop, one
+ * 1024-thread CTA per SM), the denominators of the forward's roofline. The
+ * paper has no counterpart (it reports no timings); these are the peaks of
+ * the GPU the library runs on. Shared reductions use the forward's histogram
+ * layout ([row][32] words, lane l on bank l, rows differing per lane). */
+typedef struct {
+  uint32_t struct_size;       /* set by the caller to sizeof(nlos_peaks) */
+  int32_t num_sms;
+  double ffma;                /* scalar FP32 fma */
+  double ffma2;               /* packed FP32x2 fma (two per lane and instruction) */
+  double sqrt_approx;         /* MUFU square root estimate */
+  double rcp_approx;          /* MUFU reciprocal estimate */
+  double rsqrt_approx;        /* MUFU reciprocal square root estimate */
+  double lds128_broadcast;    /* 16-byte shared loads, one address per warp (lanes) */
+  double red_f32;             /* red.shared.add.f32, all 32 lanes active */
+  double red_u32;             /* red.shared.add.u32, all lanes */
+  double red_u64;             /* red.shared.add.u64, all lanes (8-byte words) */
+  double rmw_f32;             /* non-atomic shared load + add + store, all lanes */
+  double red_f32_quarter;     /* red.shared.add.f32 with one lane in four active */
+  double red_u32_quarter;     /* red.shared.add.u32 with one lane in four active */
+} nlos_peaks;
+
+/* Runs the microbenchmarks on the current device (about a second; waits for
+ * cuda_stream). Allocates a small stream-ordered scratch. */
+nlos_status nlos_measure_peaks(nlos_peaks* out, void* cuda_stream);
 
 /* ---- Misc ---------------------------------------------------------------- */
 

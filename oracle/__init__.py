@@ -137,6 +137,7 @@ def _load():
             lib.orc_jitter_padded.argtypes = [_P, _I64, ctypes.c_int32, _P, ctypes.c_int32,
                                               ctypes.c_int32, _P]
             lib.orc_philox4x32_10.argtypes = [_P, _P, _P]
+            lib.orc_philox_many.argtypes = [_P, _I64, _P, _P]
             lib.orc_noise_lambda.argtypes = [_P, _I64, ctypes.c_float, ctypes.c_float, _P]
             lib.orc_poisson_one.argtypes = [ctypes.c_float, ctypes.c_uint64, ctypes.c_uint64,
                                             ctypes.c_uint32]
@@ -298,8 +299,7 @@ def philox(ctr: np.ndarray, key) -> np.ndarray:
     c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
     k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
     out = np.zeros_like(c)
-    for i in range(c.shape[0]):
-        lib.orc_philox4x32_10(_ptr(c[i]), _ptr(k), _ptr(out[i]))
+    lib.orc_philox_many(_ptr(c), c.shape[0], _ptr(k), _ptr(out))
     return out
 
 
@@ -323,8 +323,11 @@ def noise_lambda(tau_g: np.ndarray, params: dict):
 
     peak mode (Eq. 18 with a photon budget): scale = peak_photons / max(tau_G),
     lambda = scale * tau_G + dark.  Paper mode (Eq. 18/19, Algorithm 1):
-    sigma_n = Var(tau_G) / 10^(nr/10) over the whole cube, lambda = sigma_n *
-    tau_G (the noisy result is counts / sigma_n)."""
+    sigma_n = Var(tau_G) / 10^(nr/10) over the whole cube (population
+    variance), lambda = sigma_n * tau_G + dark (the noisy result is counts /
+    sigma_n; dark counts add to lambda in both modes, a sum of Poisson
+    variables being Poisson).  Both scales are taken over the whole cube given,
+    not per transient."""
     t32 = np.asarray(tau_g, dtype=np.float32)
     if params["noise_mode"] == "peak":
         peak = float(np.max(t32)) if t32.size else 0.0
@@ -333,7 +336,7 @@ def noise_lambda(tau_g: np.ndarray, params: dict):
     elif params["noise_mode"] == "paper_nr":
         var = float(np.var(np.asarray(tau_g, dtype=np.float64)))
         scale = np.float32(var / (10.0 ** (float(params["nr_db"]) / 10.0)))
-        dark = np.float32(0.0)
+        dark = np.float32(params["dark_per_bin"])
     else:
         raise ValueError("noise disabled")
     lam = lam_from(tau_g, scale, dark)

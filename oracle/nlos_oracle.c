@@ -379,6 +379,12 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+/* The same generator over n counters ([n][4] words) under one key (a loop
+ * over orc_philox4x32_10, so that tests can compare millions of words). */
+void orc_philox_many(const uint32_t* ctr, int64_t n, const uint32_t key[2], uint32_t* out) {
+  for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
 /* ---------------------------------------------------------------------------
  * Per-bin random stream: key = (seed_lo, seed_hi), counter =
  * (index_lo, index_hi, block, stream_tag), where index is the global bin index

@@ -92,6 +92,7 @@ void orc_jitter_padded(const double* tau, int64_t num_traces, int32_t num_bins,
 
 /* Philox4x32-10 (Salmon et al., SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_philox_many(const uint32_t* ctr, int64_t n, const uint32_t key[2], uint32_t* out);
 
 /* Poisson noise (Eq. 18/19, Algorithm 1 step 2.4). */
 void orc_noise_lambda(const double* tau_g, int64_t n, float scale, float dark, float* lam);

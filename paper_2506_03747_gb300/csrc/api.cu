@@ -13,9 +13,14 @@ namespace nlos {
 
 nlos_status scene_create(const nlos_params* params, const float* pts, uint64_t P, int on_device,
                          cudaStream_t st, nlos_scene** out);
+nlos_status scene_create_rows(const nlos_params* params, const float* pts, uint64_t P,
+                              int on_device, uint32_t row_begin, uint32_t row_count,
+                              cudaStream_t st, nlos_scene** out);
 nlos_status scene_destroy(nlos_scene* sc);
 nlos_status scene_set_points(nlos_scene* sc, const float* pts, uint64_t P, int on_device,
                              cudaStream_t st);
+nlos_status scene_set_albedo_depth(nlos_scene* sc, const float* albedo, const float* depth,
+                                   cudaStream_t st);
 
 namespace {
 thread_local std::string g_last_error;
@@ -38,6 +43,9 @@ namespace {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Global index of the scene's first bin in the whole cube (its Philox streams).
+uint64_t first_bin(const Geometry& g) { return (uint64_t)g.row0 * g.nx * g.B; }
 
 }  // namespace
 
@@ -104,10 +112,30 @@ nlos_status nlos_scene_shape(const nlos_scene* scene, uint64_t* num_scan, uint32
   return NLOS_OK;
 }
 
+nlos_status nlos_scene_create_rows(const nlos_params* params, const float* points_aos8,
+                                   uint64_t num_points, int points_on_device, uint32_t row_begin,
+                                   uint32_t row_count, void* cuda_stream, nlos_scene** out) {
+  clear_error();
+  try {
+    return scene_create_rows(params, points_aos8, num_points, points_on_device, row_begin,
+                             row_count, as_stream(cuda_stream), out);
+  } catch (...) {
+    return set_error(NLOS_ENOMEM, "host allocation failed");
+  }
+}
+
 nlos_status nlos_scene_set_points(nlos_scene* scene, const float* points_aos8, uint64_t num_points,
                                   int points_on_device, void* cuda_stream) {
   clear_error();
   return scene_set_points(scene, points_aos8, num_points, points_on_device, as_stream(cuda_stream));
+}
+
+nlos_status nlos_scene_set_albedo_depth(nlos_scene* scene, const float* albedo_dev,
+                                       const float* depth_dev, void* cuda_stream) {
+  clear_error();
+  if ((albedo_dev && !aligned16(albedo_dev)) || (depth_dev && !aligned16(depth_dev)))
+    return set_error(NLOS_EINVAL, "albedo_dev and depth_dev must be 16-byte aligned");
+  return scene_set_albedo_depth(scene, albedo_dev, depth_dev, as_stream(cuda_stream));
 }
 
 nlos_status nlos_scene_set_occluders(nlos_scene* scene, const float* occluders, uint32_t count,
@@ -194,7 +222,27 @@ nlos_status nlos_detect(nlos_scene* scene, const float* tau_dev, uint32_t* count
     NLOS_CUDA_TRY(launch_noise_scene(tau_dev, g.S * (uint64_t)g.B, s.scratch, g.noise_mode,
                                      s.params.peak_photons, s.params.dark_per_bin,
                                      s.params.nr_db, s.params.seed, s.params.stream_tag,
-                                     counts_dev, st));
+                                     counts_dev, st, first_bin(g)));
+  return NLOS_OK;
+}
+
+nlos_status nlos_noise_part(nlos_scene* scene, const float* tau_dev, uint32_t* counts_dev,
+                            const double* cube_stats_dev, uint64_t cube_bins, void* cuda_stream) {
+  clear_error();
+  if (!scene) return set_error(NLOS_EINVAL, "scene is NULL");
+  SceneImpl& s = scene->impl;
+  const Geometry& g = s.g;
+  if (!tau_dev || !aligned16(tau_dev) || !counts_dev || !aligned16(counts_dev))
+    return set_error(NLOS_EINVAL, "tau_dev and counts_dev must be 16-byte aligned device pointers");
+  if (!cube_stats_dev) return set_error(NLOS_EINVAL, "cube_stats_dev is NULL");
+  if (g.noise_mode == NLOS_NOISE_NONE) return set_error(NLOS_EINVAL, "noise_mode is NONE");
+  if (cube_bins < g.S * (uint64_t)g.B)
+    return set_error(NLOS_EINVAL, "cube_bins is smaller than the scene's own bins");
+  NLOS_CUDA_TRY(launch_noise_scene(tau_dev, g.S * (uint64_t)g.B, s.scratch, g.noise_mode,
+                                   s.params.peak_photons, s.params.dark_per_bin, s.params.nr_db,
+                                   s.params.seed, s.params.stream_tag, counts_dev,
+                                   as_stream(cuda_stream), first_bin(g), cube_stats_dev,
+                                   cube_bins));
   return NLOS_OK;
 }
 

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256)
 
   const uint64_t s = tile * kBwdTile + lane;
   const bool valid = s < a.S;
-  ScanPoint sp = valid ? a.scan[s] : ScanPoint{0.f, 0.f, -1e30f, 0.f};
+  ScanPoint sp = valid ? a.scan[s] : ScanPoint{0.f, 0.f, -1e30f, 0u};
   const float dx_s = sp.sx, dy_s = sp.sy;
   const float lx = a.scan_mode == NLOS_CONFOCAL ? sp.sx : a.lx;
   const float ly = a.scan_mode == NLOS_CONFOCAL ? sp.sy : a.ly;

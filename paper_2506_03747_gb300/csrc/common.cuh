@@ -49,10 +49,21 @@ struct __align__(16) PointPair {
 };
 static_assert(sizeof(PointPair) == 64, "PointPair must be 64 bytes");
 
-// Per-scan-point record: spot (sx, sy), bin offset off_s = (legs(s) - L0)/(c dt).
+// Per-scan-point record: spot (sx, sy), bin offset off_s = (legs(s) - L0)/(c dt),
+// and the transient's row in the caller's [scan_ny][scan_nx] layout. The
+// forward reads its scan table in tile order (compact_tile_order), so that
+// the 32 spots of a tile cover a compact 8 x 4 patch of the wall and its
+// bounds rule out more (tile, point block) units.
 struct __align__(16) ScanPoint {
-  float sx, sy, off, pad;
+  float sx, sy, off;
+  uint32_t row;
 };
+
+// Scan points in tile order: 8 x 4 patches of the grid (x fastest), patches
+// row by row; grids that are not multiples of the patch fill the last tiles
+// of each patch row with the ragged remainder. out[k] = plain[order[k]].
+void compact_tile_order(const std::vector<ScanPoint>& plain, uint32_t nx, uint32_t ny,
+                        std::vector<ScanPoint>& out);
 
 // Bounds of one sub-block of kSubPairs packed pairs (2 * kSubPairs points,
 // in packed order), for the forward's unit culling:
@@ -103,8 +114,10 @@ constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
 static_assert(sizeof(SceneScratch) == 80, "scratch layout");
 
 struct Geometry {
-  // host-side resolved parameters
+  // host-side resolved parameters; a scene may hold scan rows [row0, row0 + ny)
+  // of a grid of ny_full rows (a part of a cube split over devices)
   uint32_t nx, ny, B;
+  uint32_t row0 = 0, ny_full = 0;
   uint64_t S, P;
   int scan_mode, cos_mode, bin_mode, noise_mode;
   double cdt;        // c * dt [m]
@@ -136,10 +149,15 @@ cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double*
 cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,
                          uint32_t stream_tag, uint64_t index_base, uint32_t* counts,
                          cudaStream_t st);
-// Noise for a scene: scale from the scene's reduction results (scratch).
+// Noise for a scene: scale from the scene's reduction results (scratch), or,
+// for a part of a larger cube, from the whole cube's {max, sum, sumsq}
+// (cube_stats, device) over cube_bins bins; Philox streams of the global bin
+// indices index_base + i.
 cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scratch, int mode,
                                float peak_photons, float dark, float nr_db, uint64_t seed,
-                               uint32_t stream_tag, uint32_t* counts, cudaStream_t st);
+                               uint32_t stream_tag, uint32_t* counts, cudaStream_t st,
+                               uint64_t index_base = 0, const double* cube_stats = nullptr,
+                               uint64_t cube_bins = 0);
 cudaError_t launch_philox(const uint32_t* ctr, uint64_t n, uint32_t k0, uint32_t k1,
                           uint32_t* out, cudaStream_t st);
 
@@ -159,14 +177,16 @@ struct SceneImpl {
   nlos_params params;
   Geometry g;
   PointPair* pairs = nullptr;      // [ceil(P/2)] in spatial order
-  ScanPoint* scan = nullptr;       // [S padded to the scan tile]
+  ScanPoint* scan = nullptr;       // [S] in scan order (adjoint, pair table)
+  ScanPoint* scan_fwd = nullptr;   // [S] in tile order (forward)
   SceneScratch* scratch = nullptr; // device
-  float* raw_points = nullptr;     // [P][8] original records (for the adjoint)
+  float* raw_points = nullptr;     // [P][8] records the scene simulates (for the adjoint)
+  float* base_points = nullptr;    // [P][8] records as given, once set_albedo_depth is used
   uint32_t* perm = nullptr;        // [P] packed position -> original point index
   uint16_t* cell = nullptr;        // [P] Morton cell of each point (ordering scratch)
   uint32_t* cells = nullptr;       // [kOrderCells + 8] counts/cursors + box (ordering scratch)
   BlockBound* bounds = nullptr;    // [ceil(P / 2 / kSubPairs)]
-  TileBound* tiles = nullptr;      // [ceil(S / kTile)]
+  TileBound* tiles = nullptr;      // [ceil(S / kTile)] of scan_fwd
   OccSet occ{};                    // occluders (host copy; n = 0: none)
   cudaStream_t stream = nullptr;   // creation stream
   int device = 0;

@@ -108,11 +108,19 @@ cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t
 
 // ---------------------------------------------------------------------------
 // Reductions: one warp per transient. energy[t] = sum_b tau[t][b] in FP64;
-// cube maximum via atomicMax on the float bits (tau >= 0 orders like its
-// bits); FP64 sum and sum of squares via one double atomicAdd per warp.
+// the cube's maximum, FP64 sum and sum of squares are combined per CTA in
+// shared memory, then one atomicMax on the float bits (tau >= 0 orders like
+// its bits) and two double atomicAdds per CTA (per-warp atomics on the same
+// three words serialised in L2).
 // ---------------------------------------------------------------------------
-__global__ void reduce_kernel(const float* __restrict__ tau, uint64_t traces, uint32_t B,
-                              double* energy, SceneScratch* scratch) {
+constexpr int kReduceThreads = 256;
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const float* __restrict__ tau,
+                                                                uint64_t traces, uint32_t B,
+                                                                double* energy,
+                                                                SceneScratch* scratch) {
+  __shared__ double s_sum[kReduceThreads / 32], s_sq[kReduceThreads / 32];
+  __shared__ float s_max[kReduceThreads / 32];
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   double csum = 0.0, csq = 0.0;
@@ -149,7 +157,20 @@ __global__ void reduce_kernel(const float* __restrict__ tau, uint64_t traces, ui
     csq += q;
     cmax = fmaxf(cmax, m);
   }
-  if (lane == 0 && scratch) {
+  if (!scratch) return;
+  const int warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_sum[warp] = csum;
+    s_sq[warp] = csq;
+    s_max[warp] = cmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      csum += s_sum[w];
+      csq += s_sq[w];
+      cmax = fmaxf(cmax, s_max[w]);
+    }
     atomicMax(&scratch->peak_bits, __float_as_uint(cmax));
     atomicAdd(&scratch->sum, csum);
     atomicAdd(&scratch->sumsq, csq);
@@ -164,7 +185,7 @@ cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double*
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t want = (traces + 7) / 8;
   const unsigned blocks = (unsigned)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
-  reduce_kernel<<<blocks, 256, 0, st>>>(tau, traces, B, energy, scratch);
+  reduce_kernel<<<blocks, kReduceThreads, 0, st>>>(tau, traces, B, energy, scratch);
   return cudaGetLastError();
 }
 
@@ -179,11 +200,28 @@ struct NoiseArgs {
   SceneScratch* scratch;      // else: scale from the reduced cube
   int mode;                   // nlos_noise_mode (scratch path)
   float peak_photons, dark_cfg, nr_db;
+  const double* cube_stats;   // part of a larger cube: {max, sum, sumsq} of the whole
+  uint64_t cube_bins;         // bins of the whole cube
 };
 
-__global__ void noise_kernel(const NoiseArgs a) {
+// One resident wave (kNoiseBlocksPerSm CTAs of 256 threads per SM, register
+// budget set by the launch bounds) walks the bins with a grid stride; each
+// thread loads its next bin's tau before sampling the current one, so the
+// HBM latency overlaps the Philox rounds.
+constexpr int kNoiseThreads = 256;
+constexpr int kNoiseBlocksPerSm = 8;
+
+__global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
   float scale = a.scale, dark = a.dark;
-  if (a.scratch) {
+  if (a.cube_stats) {
+    scale = noise_scale_of((float)a.cube_stats[0], a.cube_stats[1], a.cube_stats[2], a.mode,
+                           a.peak_photons, a.nr_db, a.cube_bins);
+    dark = a.dark_cfg;
+    if (a.scratch && blockIdx.x == 0 && threadIdx.x == 0) {
+      a.scratch->scale = scale;
+      a.scratch->dark = dark;
+    }
+  } else if (a.scratch) {
     scale = noise_scale_from(a.scratch, a.mode, a.peak_photons, a.nr_db, a.n);
     dark = a.dark_cfg;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -192,9 +230,16 @@ __global__ void noise_kernel(const NoiseArgs a) {
     }
   }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const float lam = fmaf(scale, __ldg(a.tau + i), dark);
-    a.counts[i] = poisson_sample(lam, a.index_base + i, a.seed, a.tag);
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  float t = __ldg(a.tau + i);
+  for (;;) {
+    const uint64_t next = i + stride;
+    const float t_next = next < a.n ? __ldg(a.tau + next) : 0.0f;
+    a.counts[i] = poisson_sample(fmaf(scale, t, dark), a.index_base + i, a.seed, a.tag);
+    if (next >= a.n) break;
+    i = next;
+    t = t_next;
   }
 }
 
@@ -203,9 +248,10 @@ cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = (a.n + 255) / 256;
-  const unsigned blocks = (unsigned)(want < (uint64_t)sms * 16 ? want : (uint64_t)sms * 16);
-  noise_kernel<<<blocks, 256, 0, st>>>(a);
+  const uint64_t want = (a.n + kNoiseThreads - 1) / kNoiseThreads;
+  const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm;
+  const unsigned blocks = (unsigned)(want < wave ? want : wave);
+  noise_kernel<<<blocks, kNoiseThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -226,12 +272,16 @@ cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, 
 
 cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scratch, int mode,
                                float peak_photons, float dark, float nr_db, uint64_t seed,
-                               uint32_t tag, uint32_t* counts, cudaStream_t st) {
+                               uint32_t tag, uint32_t* counts, cudaStream_t st,
+                               uint64_t index_base, const double* cube_stats,
+                               uint64_t cube_bins) {
   NoiseArgs a{};
   a.tau = tau;
   a.counts = counts;
   a.n = n;
-  a.index_base = 0;
+  a.index_base = index_base;
+  a.cube_stats = cube_stats;
+  a.cube_bins = cube_bins;
   a.seed = seed;
   a.tag = tag;
   a.scratch = scratch;

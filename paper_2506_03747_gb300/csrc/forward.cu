@@ -160,7 +160,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
 
   FwdArgs a{};
   a.pairs = sc.pairs;
-  a.scan = sc.scan;
+  a.scan = sc.scan_fwd;
   a.tau = tau;
   a.err = &sc.scratch->err;
   a.boundary = &sc.scratch->boundary_pairs;

@@ -150,18 +150,20 @@ __device__ __forceinline__ void pair_geom2(const PointPair& q, float2 nsx, float
   cn = __ffma2_rn(q.nb, dy, cn);
 }
 
-// u is formed relative to bin 0 of the transient and then moved to the
-// window (nw0 = -w0: an exact subtraction of an integer below 2^24), so the
-// bins and splat taps of a pair do not depend on how the bins are windowed.
+// u is formed relative to bin 0 of the transient; callers move it to the
+// window by an exact subtraction of the window's first bin (an integer below
+// 2^24: in the float for the splat forms, in the integer bin for the binned
+// ones), so the bins and splat taps of a pair do not depend on how the bins
+// are windowed.
 template <int SCAN, int COS>
 __device__ __forceinline__ void pair_finish2(const PointPair& q, float2 r2, float2 cn, float2 off,
-                                             float2 kbin, float2 nw0, float2& u, float2& w) {
+                                             float2 kbin, float2& u, float2& w) {
   const float2 o = (SCAN == NLOS_CONFOCAL) ? off : __fadd2_rn(off, q.uoff);
 #if NLOS_FWD_SQRT_RCP
   // r from the hardware square root; the weight's inverse powers of r from a
   // single reciprocal of r^2k, so no approximation error is raised to a power
   const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
-  u = __fadd2_rn(__ffma2_rn(r, kbin, o), nw0);
+  u = __ffma2_rn(r, kbin, o);
   if (SCAN == NLOS_CONFOCAL) {
     if (COS == NLOS_COS_NONE) {
       const float2 d = __fmul2_rn(r2, r2);
@@ -193,7 +195,7 @@ __device__ __forceinline__ void pair_finish2(const PointPair& q, float2 r2, floa
   const float2 e = __ffma2_rn(make_float2(-r.x, -r.y), ri, make_float2(1.0f, 1.0f));
   ri = __ffma2_rn(__fmul2_rn(ri, make_float2(0.5f, 0.5f)), e, ri);
   r = __fmul2_rn(r2, ri);
-  u = __fadd2_rn(__ffma2_rn(r, kbin, o), nw0);
+  u = __ffma2_rn(r, kbin, o);
   float2 ri2 = __fmul2_rn(ri, ri);
   if (SCAN == NLOS_CONFOCAL) {
     if (COS == NLOS_COS_NONE) {
@@ -222,7 +224,7 @@ __device__ __forceinline__ void pair_eval2(const PointPair& q, float2 nsx, float
                                            float2 kbin, float2& u, float2& w, float2& cn) {
   float2 r2;
   pair_geom2(q, nsx, nsy, r2, cn);
-  pair_finish2<SCAN, COS>(q, r2, cn, off, kbin, make_float2(0.f, 0.f), u, w);
+  pair_finish2<SCAN, COS>(q, r2, cn, off, kbin, u, w);
 }
 
 // Early-out test on r^2, before any square root: can the point land in
@@ -315,6 +317,7 @@ struct TileState {
   float2 sx2, sy2, nsx2, nsy2;
   float2 off2;          // bin offset of the scan point, relative to bin 0
   float2 nw02;          // -(first bin of the window)
+  uint32_t binbase = kMagicBits;  // bit pattern of kMagic + first bin of the window
   float2 r2lo2, r2hi2;  // early-out bounds (see may_bin2)
 };
 
@@ -342,6 +345,7 @@ __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int la
     ts.nsy2 = make_float2(-sp.sy, -sp.sy);
     ts.off2 = make_float2(sp.off, sp.off);
     ts.nw02 = make_float2(-(float)ts.w0, -(float)ts.w0);
+    ts.binbase = (uint32_t)kMagicBits + ts.w0;
     const float o = sp.off - (float)ts.w0;
     // r range of u in [-margin, lim + margin): r = (u - o) / kbin
     const float ik = 1.0f / a.kbin;
@@ -360,6 +364,7 @@ __device__ __forceinline__ void load_tile(const FwdArgs& a, long long tw, int la
     ts.sx2 = ts.sy2 = ts.nsx2 = ts.nsy2 = make_float2(0.f, 0.f);
     ts.off2 = make_float2(-1e30f, -1e30f);  // u -> -inf: never binned
     ts.nw02 = make_float2(0.f, 0.f);
+    ts.binbase = (uint32_t)kMagicBits + ts.w0;
     ts.r2lo2 = make_float2(1.f, 1.f);      // empty r ranges
     ts.r2hi2 = make_float2(-1.f, -1.f);
   }
@@ -454,7 +459,10 @@ __device__ __forceinline__ void flush_tile(const FwdArgs& a, long long tw, const
   if (hi <= lo) return;
   const int nq = (hi - lo + 3) >> 2;  // quads of output bins
   const int c = threadIdx.x & 31;
-  const uint32_t s = tile * kTile + c;
+  // the transient (output row) of the lane's scan point; none for the padding
+  // lanes of a ragged last tile
+  const uint32_t si = tile * kTile + c;
+  const uint32_t s = si < a.S ? a.scan[si].row : 0xFFFFFFFFu;
 #define NLOS_FLUSH_R(RR) \
   case RR:               \
     flush_quads<RR>(a, hist, lo, nq, w0, R, s, c, warp_rel, n_warps); \
@@ -562,13 +570,18 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
   const float2 kbin2 = make_float2(a.kbin, a.kbin);
   const float2 magic2 = make_float2(kMagic, kMagic);
   const float2 ikbin_neg = make_float2(-1.0f / a.kbin, -1.0f / a.kbin);
+  // iterations of this warp (counted once per block, not per iteration)
+  const uint32_t n_it = n > (uint32_t)warp_rel ? (n - 1u - (uint32_t)warp_rel) / (uint32_t)n_warps + 1u : 0u;
+  cnt.tested += n_it;
+#if !NLOS_FWD_EARLY
+  cnt.full += n_it;
+#endif
 #pragma unroll UNROLL
   for (uint32_t i = warp_rel; i < n; i += n_warps) {
     PointPair q;
     load_pair(blkp + i, q);
     float2 r2, cn;
     pair_geom2(q, ts.nsx2, ts.nsy2, r2, cn);
-    ++cnt.tested;
 #if NLOS_FWD_EARLY
     // warp-uniform early out: for most (tile, point) combinations of a
     // scene no lane can bin either point (outside the window or facing away).
@@ -579,10 +592,12 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
       if (!__any_sync(0xffffffffu, (m.x && facing<COS>(cn.x)) || (m.y && facing<COS>(cn.y))))
         continue;
     }
-#endif
     ++cnt.full;
+#endif
     float2 u, w;
-    pair_finish2<SCAN, COS>(q, r2, cn, ts.off2, kbin2, ts.nw02, u, w);
+    pair_finish2<SCAN, COS>(q, r2, cn, ts.off2, kbin2, u, w);
+    // window-relative u for the splat forms (exact: w0 is an integer < 2^24)
+    if (MODE == MODE_SPLAT || MODE == MODE_SPLAT_MOM) u = __fadd2_rn(u, ts.nw02);
     if (MODE == MODE_SPLAT) {
       if (facing<COS>(cn.x)) splat_one(col_addr, u.x, w.x, ts.lim, a);
       if (facing<COS>(cn.y)) splat_one(col_addr, u.y, w.y, ts.lim, a);
@@ -608,9 +623,11 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
       red_moments<COS>(col_addr + rb * (kTile * 4), w.y, c.y, rb, rows, cn.y);
 #endif
     } else {
-      const float2 t = __fadd2_rd(u, magic2);  // kMagic + floor(u), exactly
-      uint32_t ba = (uint32_t)(__float_as_int(t.x) - kMagicBits);
-      uint32_t bb = (uint32_t)(__float_as_int(t.y) - kMagicBits);
+      // kMagic + floor(u), exactly; the window's first bin comes off the
+      // integer (floor(u) - w0 = floor(u - w0) for an integer w0)
+      const float2 t = __fadd2_rd(u, magic2);
+      uint32_t ba = (uint32_t)__float_as_int(t.x) - ts.binbase;
+      uint32_t bb = (uint32_t)__float_as_int(t.y) - ts.binbase;
       if (MODE == MODE_NEAREST_OCC) {
         // visibility only for pairs that would be binned; a hidden pair's bin
         // is moved out of range, so its reduction is predicated off
@@ -680,7 +697,10 @@ __device__ __forceinline__ void flush_tile_mom(const FwdArgs& a, const MomTab& m
   const int J = mt.J;
   const int nq = (lim + 3) >> 2;
   const int c = threadIdx.x & 31;
-  const uint32_t s = tile * kTile + c;
+  // the transient (output row) of the lane's scan point; none for the padding
+  // lanes of a ragged last tile
+  const uint32_t si = tile * kTile + c;
+  const uint32_t s = si < a.S ? a.scan[si].row : 0xFFFFFFFFu;
   for (int qi = warp_rel; qi < nq; qi += n_warps) {
     const int r0 = 4 * qi;  // window-relative output bin
     float v[4] = {0.f, 0.f, 0.f, 0.f};

@@ -65,7 +65,10 @@ __device__ inline uint32_t poisson_knuth(float lam, BinStream& st) {
   return k;
 }
 
-__device__ inline uint32_t poisson_ptrs(float lam_f, BinStream& st) {
+// Out of line: the PTRS range is rare (lambda >= 150), and inlined it would
+// set the register budget of every bin's path. The stream is passed by value
+// (it is the bin's last sampler), so it stays in registers on both sides.
+static __device__ __noinline__ uint32_t poisson_ptrs(float lam_f, BinStream st) {
   const double lam = (double)lam_f;
   const double slam = sqrt(lam);
   const double loglam = log(lam);
@@ -108,18 +111,22 @@ __device__ __forceinline__ uint32_t poisson_sample(float lam, uint64_t index, ui
 
 // Noise scale from a cube's reduction results (identical in every thread):
 //  PEAK:     scale = peak_photons / max tau_G (0 for an empty cube);
-//  PAPER_NR: scale = sigma_n = Var(tau_G) / 10^(nr/10), population variance.
-__device__ __forceinline__ float noise_scale_from(const SceneScratch* sc, int mode,
-                                                  float peak_photons, float nr_db, uint64_t n) {
-  if (mode == NLOS_NOISE_PEAK) {
-    const float peak = __uint_as_float(sc->peak_bits);
-    return peak > 0.0f ? __fdiv_rn(peak_photons, peak) : 0.0f;
-  }
+//  PAPER_NR: scale = sigma_n = Var(tau_G) / 10^(nr/10), population variance
+//            over the n bins of the whole cube.
+__device__ __forceinline__ float noise_scale_of(float peak, double sum, double sumsq, int mode,
+                                                float peak_photons, float nr_db, uint64_t n) {
+  if (mode == NLOS_NOISE_PEAK) return peak > 0.0f ? __fdiv_rn(peak_photons, peak) : 0.0f;
   const double nn = (double)n;
-  const double mean = sc->sum / nn;
-  double var = sc->sumsq / nn - mean * mean;
+  const double mean = sum / nn;
+  double var = sumsq / nn - mean * mean;
   if (var < 0.0) var = 0.0;
   return (float)(var / pow(10.0, (double)nr_db / 10.0));
+}
+
+__device__ __forceinline__ float noise_scale_from(const SceneScratch* sc, int mode,
+                                                  float peak_photons, float nr_db, uint64_t n) {
+  return noise_scale_of(__uint_as_float(sc->peak_bits), sc->sum, sc->sumsq, mode, peak_photons,
+                        nr_db, n);
 }
 
 }  // namespace nlos

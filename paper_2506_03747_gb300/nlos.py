@@ -77,6 +77,16 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "struct_size"}
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("num_sms", ctypes.c_int32)] + [
+        (n, ctypes.c_double) for n in (
+            "ffma", "ffma2", "sqrt_approx", "rcp_approx", "rsqrt_approx", "lds128_broadcast",
+            "red_f32", "red_u32", "red_u64", "rmw_f32", "red_f32_quarter", "red_u32_quarter")]
+
+    def to_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "struct_size"}
+
+
 _lock = threading.Lock()
 _lib = None
 _P = ctypes.c_void_p
@@ -107,6 +117,7 @@ def load(path: str | None = None):
                                      ctypes.POINTER(_U64)]),
             "nlos_simulate": (S, [_P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
             "nlos_scene_set_points": (S, [_P, _P, _U64, ctypes.c_int, _P]),
+            "nlos_scene_set_albedo_depth": (S, [_P, _P, _P, _P]),
             "nlos_scene_set_occluders": (S, [_P, _P, _U32, _P]),
             "nlos_scene_check": (S, [_P, _P]),
             "nlos_forward": (S, [_P, _P, _P]),
@@ -136,6 +147,7 @@ def load(path: str | None = None):
                                     ctypes.POINTER(ctypes.c_void_p)]),
             "nlos_lct_forward": (S, [_P, _P, _P, _P, _P]),
             "nlos_lct_destroy": (S, [_P]),
+            "nlos_measure_peaks": (S, [ctypes.POINTER(Peaks), _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -222,6 +234,7 @@ class Scene:
         self.handle = handle
         self.num_scan, self.num_bins, self.num_points = S, B, P
         self.params = prm
+        self.version = 0  # bumped by every scene_set_albedo_depth
 
     def destroy(self):
         if self.handle:
@@ -280,6 +293,19 @@ def scene_set_points(scene: Scene, points, stream=None):
     n = points.shape[0]
     _check(_lib.nlos_scene_set_points(scene.handle, _ptr(points) if n else None, n, on_dev,
                                       _stream(stream)))
+
+
+def scene_set_albedo_depth(scene: Scene, albedo=None, depth=None, stream=None):
+    """Albedo [P] and normal-offset depth [P] (float32 CUDA tensors, each
+    optional) applied to the scene's given records on the device."""
+    for t in (albedo, depth):
+        if t is not None and (not getattr(t, "is_cuda", False) or t.dtype.__str__() != "torch.float32"
+                              or not t.is_contiguous() or t.numel() != scene.num_points):
+            raise ValueError("albedo and depth must be contiguous float32 CUDA tensors of "
+                             "num_points elements")
+    _check(_lib.nlos_scene_set_albedo_depth(scene.handle, _ptr(albedo), _ptr(depth),
+                                            _stream(stream)))
+    scene.version += 1
 
 
 def scene_set_occluders(scene: Scene, occluders, stream=None):
@@ -429,10 +455,6 @@ def server_destroy(server: Server):
     server.destroy()
 
 
-def jitter_sigma_bins(fwhm_s: float, bin_width_s: float) -> float:
-    return fwhm_s / (2.0 * math.sqrt(2.0 * math.log(2.0)) * bin_width_s)
-
-
 class Lct:
     """Owning handle of an ``nlos_lct`` plan (the paper's FFT forward model)."""
 
@@ -459,3 +481,12 @@ class Lct:
         except Exception:
             pass
 
+
+def measure_peaks(stream=None) -> dict:
+    """Element operations per SM clock per SM of the units the forward is bound
+    by (``nlos_measure_peaks``); waits for the stream."""
+    lib = load()
+    pk = Peaks()
+    pk.struct_size = ctypes.sizeof(Peaks)
+    _check(lib.nlos_measure_peaks(ctypes.byref(pk), _stream(stream)))
+    return pk.to_dict()

@@ -71,6 +71,12 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert lib.nlos_simulate(None, None, None, None, None, None) == nlos.EINVAL
     assert lib.nlos_scene_set_occluders(None, None, 0, None) == nlos.EINVAL
     assert b"scene is NULL" in nlos.load().nlos_last_error()
+    assert lib.nlos_scene_set_albedo_depth(None, None, None, None) == nlos.EINVAL
+    assert b"scene is NULL" in nlos.load().nlos_last_error()
+    assert lib.nlos_measure_peaks(None, None) == nlos.EINVAL
+    pk = nlos.Peaks()
+    pk.struct_size = 8  # too small for the struct: rejected before any device work
+    assert lib.nlos_measure_peaks(ctypes.byref(pk), None) == nlos.EINVAL
     assert lib.nlos_abi_version() == 1
 
 

@@ -83,6 +83,26 @@ def _wait(srv, ticket, timeout_s=60.0):
         assert time.time() - t0 < timeout_s, "request did not finish"
 
 
+def _served_vs_oracle(prm, pts, tau, seed, n_sample=6):
+    import oracle
+    S, B = tau.shape
+    rng = np.random.default_rng(seed)
+    rows = np.unique(np.r_[rng.choice(S, size=min(S, n_sample), replace=False), S // 2])
+    for s in rows:
+        s = int(s)
+        what = f"served vs oracle s={s} ({prm['scan_nx']}x{prm['scan_ny']}x{B}, {prm['bin_mode']})"
+        if prm["bin_mode"] == "splat":
+            o = oracle.forward_splat(prm, pts, s, 1)
+            H.check_bins(tau[s:s + 1], o, what=what)
+            continue
+        o = H.oracle_with_allowance(prm, pts, s, 1)
+        H.check_bins(tau[s:s + 1], o["tau_g"], allow=o["flip_g"], what=what)
+        R = (o["taps"].size - 1) // 2
+        allow_e = o["edge"] + o["flip"][:, np.r_[0:R + 1, max(0, B - R - 1):B]].sum(axis=1)
+        H.check_energy(tau[s:s + 1].sum(axis=1), o["tau_g"].sum(axis=1), allow=allow_e,
+                       what=what + " energy")
+
+
 def test_served_in_a_mix_equals_alone():
     from paper_2506_03747_gb300 import nlos
     H.lib()
@@ -100,6 +120,12 @@ def test_served_in_a_mix_equals_alone():
         # round differently, so compare at the per-bin parity bar (1e-4 of peak)
         H.check_bins(tau.astype(np.float64), a_tau.astype(np.float64), rel=H.REL_BIN,
                      what=f"served vs alone ({prm['scan_nx']}x{prm['scan_ny']}x{B})")
+        # and against the definition itself (the FP64 oracle: Eq. 1 summed
+        # over pairs, then the jitter of Algorithm 1 step 2.3, or the splat) on
+        # sampled transients, at the parity bars: per bin 1e-4 of the
+        # transient's peak with the mass of pairs within the FP32 bound of a
+        # bin edge as allowance, energy 1e-6 (window-edge flips allowed)
+        _served_vs_oracle(prm, pts, tau.astype(np.float64), seed=int(t))
         if a_cnt is not None:
             cnt = _fetch(cnt_ptr, (S, B), torch.int32).view(np.uint32)
             diff = int((cnt != a_cnt).sum())

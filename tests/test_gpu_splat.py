@@ -71,30 +71,33 @@ def test_adjoint_matches_oracle_gradient(scan_mode, cos_mode, fwhm):
 
 
 def test_workload_glyph_batch_sampled():
-    """Workload 4 sizes (64x64 scan, 65,536 points, 512 bins of 8 ps, splat
-    with 60 ps FWHM), one scene: forward on sampled scan points and the
-    gradient on sampled points against the oracle."""
+    """Workload 4 at its sizes (8 scenes, each a 64x64 scan, 65,536 points,
+    512 bins of 8 ps, splat with 60 ps FWHM): for every scene, the forward on
+    sampled scan points and the gradient on sampled points against the
+    oracle."""
     from paper_2506_03747_gb300 import nlos
-    params, sc_pts, _ = scenes.workload_glyph_batch(n_scenes=1)
-    pts = sc_pts[0]
-    g = H.gpu_forward(params, pts)
+    params, sc_pts, _ = scenes.workload_glyph_batch()
+    assert len(sc_pts) == 8
     rng = np.random.default_rng(2)
-    for s in rng.choice(4096, size=4, replace=False):
-        o = oracle.forward_splat(params, pts, int(s), 1)
-        H.check_bins(g["tau"][s:s + 1], o, what=f"splat s={s}")
     S, B = 4096, 512
-    gt = rng.normal(size=(S, B)).astype(np.float32)
-    sc = nlos.scene_create(nlos.params(params), pts)
-    ga = torch.empty(sc.num_points, dtype=torch.float32, device="cuda")
-    gd = torch.empty(sc.num_points, dtype=torch.float32, device="cuda")
-    nlos.simulate_backward(sc, torch.from_numpy(gt).cuda(), ga, gd)
-    torch.cuda.synchronize()
-    sel = np.sort(rng.choice(pts.shape[0], size=64, replace=False))
-    oa, od = oracle.backward_splat(params, pts[sel], gt.astype(np.float64))
-    a = ga.cpu().numpy()[sel]
-    d = gd.cpu().numpy()[sel]
-    assert np.abs(a - oa).max() <= 1e-3 * np.abs(oa).max()
-    assert np.abs(d - od).max() <= 1e-3 * np.abs(od).max()
+    for k, pts in enumerate(sc_pts):
+        g = H.gpu_forward(params, pts)
+        for s in rng.choice(S, size=3, replace=False):
+            o = oracle.forward_splat(params, pts, int(s), 1)
+            H.check_bins(g["tau"][s:s + 1], o, what=f"scene {k} splat s={s}")
+        gt = rng.normal(size=(S, B)).astype(np.float32)
+        sc = nlos.scene_create(nlos.params(params), pts)
+        ga = torch.empty(sc.num_points, dtype=torch.float32, device="cuda")
+        gd = torch.empty(sc.num_points, dtype=torch.float32, device="cuda")
+        nlos.simulate_backward(sc, torch.from_numpy(gt).cuda(), ga, gd)
+        torch.cuda.synchronize()
+        sel = np.sort(rng.choice(pts.shape[0], size=48, replace=False))
+        oa, od = oracle.backward_splat(params, pts[sel], gt.astype(np.float64))
+        a = ga.cpu().numpy()[sel]
+        d = gd.cpu().numpy()[sel]
+        assert np.abs(a - oa).max() <= 1e-3 * np.abs(oa).max(), k
+        assert np.abs(d - od).max() <= 1e-3 * np.abs(od).max(), k
+        sc.destroy()
 
 
 def test_autograd_function_against_finite_differences():
@@ -103,18 +106,17 @@ def test_autograd_function_against_finite_differences():
     H.lib()
     params, pts = _small(n_side=16, scan=8)
     pts[:, 6] = 0.3 + 0.7 * pts[:, 6]  # keep albedo - h >= 0 for the differences
-    prm = nlos.params(params)
     P = pts.shape[0]
-    points = torch.from_numpy(pts).cuda()
+    scene = nlos.scene_create(nlos.params(params), torch.from_numpy(pts).cuda())
     albedo = torch.from_numpy(pts[:, 6].copy()).cuda().requires_grad_(True)
     depth = torch.zeros(P, device="cuda", requires_grad=True)
-    target = NlosSplat.apply(albedo.detach() * 0.9, depth.detach() + 2e-3, points, prm).detach()
-    loss = ((NlosSplat.apply(albedo, depth, points, prm) - target) ** 2).sum()
+    target = NlosSplat.apply(albedo.detach() * 0.9, depth.detach() + 2e-3, scene).detach()
+    loss = ((NlosSplat.apply(albedo, depth, scene) - target) ** 2).sum()
     loss.backward()
 
     def L(a, d):
         with torch.no_grad():
-            return float(((NlosSplat.apply(a, d, points, prm) - target) ** 2).sum())
+            return float(((NlosSplat.apply(a, d, scene) - target) ** 2).sum())
 
     rng = np.random.default_rng(4)
     for i in rng.choice(P, size=6, replace=False):
@@ -128,3 +130,52 @@ def test_autograd_function_against_finite_differences():
         d0 = depth.detach().clone(); d0[i] -= h
         fd = (L(albedo.detach(), d1) - L(albedo.detach(), d0)) / (2 * h)
         assert depth.grad[i].item() == pytest.approx(fd, rel=5e-2, abs=1e-4 * abs(loss.item()))
+
+
+def test_autograd_config4_directional_differences():
+    """NlosSplat at workload 4's size (one glyph scene: 64x64 scan, 65,536
+    points, 512 bins): one scene reused across steps, and the gradient of the
+    L2 loss against a perturbed target checked along random directions of
+    albedo and depth by central differences of the GPU forward (FP64 loss)."""
+    from paper_2506_03747_gb300.autograd import NlosSplat
+    from paper_2506_03747_gb300 import nlos
+    H.lib()
+    params, sc_pts, tgt_pts = scenes.workload_glyph_batch(n_scenes=1)
+    pts, tp = sc_pts[0], tgt_pts[0]
+    P = pts.shape[0]
+    scene = nlos.scene_create(nlos.params(params), torch.from_numpy(pts).cuda())
+    tsc = nlos.scene_create(nlos.params(params), tp)
+    target = torch.empty((scene.num_scan, scene.num_bins), dtype=torch.float32, device="cuda")
+    nlos.forward(tsc, target)
+    tsc.destroy()
+    albedo = torch.from_numpy(pts[:, 6].copy()).cuda().requires_grad_(True)
+    depth = torch.zeros(P, device="cuda", requires_grad=True)
+
+    def loss_of(a, d):
+        return ((NlosSplat.apply(a, d, scene) - target).double() ** 2).sum()
+
+    for step in range(2):  # the scene is reused: a second step sees the same state
+        albedo.grad = None
+        depth.grad = None
+        loss = loss_of(albedo, depth)
+        loss.backward()
+    rng = np.random.default_rng(9)
+    lit = pts[:, 6] > 0  # albedo moves only where it stays positive (the glyph's 1s)
+    for name, h in (("albedo", 1e-2), ("depth", 5e-5)):
+        v = rng.normal(size=P).astype(np.float32)
+        if name == "albedo":
+            v[~lit] = 0.0
+        v = torch.from_numpy(v).cuda()
+        with torch.no_grad():
+            if name == "albedo":
+                lp = float(loss_of(albedo.detach() + h * v, depth.detach()))
+                lm = float(loss_of(albedo.detach() - h * v, depth.detach()))
+                an = float((albedo.grad.double() * v.double()).sum())
+            else:
+                lp = float(loss_of(albedo.detach(), depth.detach() + h * v))
+                lm = float(loss_of(albedo.detach(), depth.detach() - h * v))
+                an = float((depth.grad.double() * v.double()).sum())
+        fd = (lp - lm) / (2 * h)
+        print(name, "directional derivative: adjoint", an, "central differences", fd)
+        assert an == pytest.approx(fd, rel=2e-2), name
+    scene.destroy()

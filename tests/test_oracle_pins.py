@@ -441,6 +441,51 @@ def test_poisson_dark_only_zero_probability_and_streams():
 
 
 # ---------------------------------------------------------------------------
+# Noise scale (Eq. 18/19, Algorithm 1 step 2.4) on a hand-worked 2 x 3 cube:
+#   tau_G = [[0, 1, 2], [4, 0.5, 3]], sum 10.5, mean 1.75.
+# PEAK: the maximum over the whole cube is 4 (per-transient maxima would be 2
+# and 4), so with 100 photons the scale is 25 and lambda = 25 tau_G + dark.
+# PAPER_NR: the squared deviations from 1.75 are 3.0625, 0.5625, 0.0625,
+# 5.0625, 1.5625, 1.5625; their sum is 11.875, so the population variance is
+# 11.875 / 6 = 95/48 (the sample variance would be 11.875 / 5 = 2.375); at
+# nr = 2 dB the scale is (95/48) / 10^0.2.
+# ---------------------------------------------------------------------------
+def test_noise_lambda_hand_worked_cube():
+    tau_g = np.array([[0.0, 1.0, 2.0], [4.0, 0.5, 3.0]])
+    p = _params(noise_mode="peak", peak_photons=100.0, dark_per_bin=1e-3)
+    lam, scale, dark = oracle.noise_lambda(tau_g, p)
+    assert scale == 25.0
+    assert dark == float(np.float32(1e-3))
+    want = np.array([[0.001, 25.001, 50.001], [100.001, 12.501, 75.001]], dtype=np.float32)
+    np.testing.assert_allclose(lam, want, rtol=2e-7, atol=0)
+    assert lam.dtype == np.float32 and lam.shape == (2, 3)
+
+    p = _params(noise_mode="paper_nr", nr_db=2.0, dark_per_bin=0.0)
+    lam, scale, dark = oracle.noise_lambda(tau_g, p)
+    sigma_n = 1.9791666666666667 / 1.5848931924611136  # (95/48) / 10^(2/10)
+    assert abs(scale - sigma_n) <= 1e-7 * sigma_n
+    assert dark == 0.0
+    np.testing.assert_allclose(lam, np.float32(sigma_n) * tau_g.astype(np.float32), rtol=2e-7)
+    # a louder setting (larger nr) gives a smaller scale: fewer counts, more noise
+    _, scale4, _ = oracle.noise_lambda(tau_g, dict(p, nr_db=4.0))
+    assert abs(scale4 - 1.9791666666666667 / 2.51188643150958) <= 1e-7 * scale4
+    # dark counts add to lambda in the paper mode as well
+    lam_d, _, dark_d = oracle.noise_lambda(tau_g, dict(p, dark_per_bin=0.25))
+    assert dark_d == 0.25
+    np.testing.assert_allclose(lam_d, lam + np.float32(0.25), rtol=2e-7)
+
+
+def test_noise_lambda_zero_cube():
+    """An empty (all-zero) cube: no scale (no division by a zero peak)."""
+    tau_g = np.zeros((3, 4))
+    lam, scale, dark = oracle.noise_lambda(tau_g, _params(noise_mode="peak", dark_per_bin=1e-3))
+    assert scale == 0.0
+    np.testing.assert_array_equal(lam, np.full((3, 4), np.float32(1e-3)))
+    lam, scale, _ = oracle.noise_lambda(tau_g, _params(noise_mode="paper_nr", dark_per_bin=0.0))
+    assert scale == 0.0 and not lam.any()
+
+
+# ---------------------------------------------------------------------------
 # Splat forward: a single pair spreads w * N(b + 1/2 - u; 0, sigma) over the
 # bins within 6 sigma (scipy's normal pdf), and the gradient matches central
 # finite differences of the FP64 forward.
