@@ -12,8 +12,11 @@ scan, 262,144 points, 512 bins of 8 ps) is reported beside it under
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank simulates its own independent scene (seed
-offset by the rank): weak scaling, no collective on the data path.
+Under torchrun (N > 1) the ranks share one cube split by scan rows (every
+rank holds all points and simulates its block of rows; one all-reduce of the
+cube's max / sums before the noise): strong scaling. With --replicas every
+rank simulates its own independent scene instead (seed offset by the rank):
+weak scaling, no collective on the data path.
 """
 from __future__ import annotations
 
@@ -267,28 +270,48 @@ def forward_roofline(name, fwd_s, st, pairs_per_step, n_sm, sm_max_mhz, peaks, S
             "tau_write_gbs": S * B * 4 / fwd_s / 1e9}
 
 
-def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=None):
+def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=None,
+                     split=False):
     """Times `steps` bench steps of one workload (scene_set_points = ingest and
     pack, forward = pair histogram with fused jitter, detect = FP64 energy,
     cube statistics and Poisson noise), inputs resident in HBM, L2 flushed
-    between steps; then the same steps end to end with host buffers."""
+    between steps; then the same steps end to end with host buffers.
+    split: the ranks share one cube, each simulating its block of scan rows
+    (paper_2506_03747_gb300.shard; one all-reduce of the cube statistics
+    before the noise); else every rank simulates its own scene."""
     import torch
-    from paper_2506_03747_gb300 import nlos
-    params, pts_np = _workload(name, rank)
+    from paper_2506_03747_gb300 import nlos, shard
+    params, pts_np = _workload(name, 0 if split else rank)
     stream = torch.cuda.current_stream()
     pts_dev = torch.from_numpy(pts_np).cuda()
-    scene = nlos.scene_create(nlos.params(params), pts_dev)
+    if split:
+        scene = shard.scene_create_part(params, pts_dev, ws, rank)
+        if scene is None:
+            raise RuntimeError("more ranks than scan rows")
+    else:
+        scene = nlos.scene_create(nlos.params(params), pts_dev)
     S, B, P = scene.num_scan, scene.num_bins, scene.num_points
+    S_cube = params["scan_nx"] * params["scan_ny"]
     tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
     counts = torch.empty((S, B), dtype=torch.int32, device="cuda")
     energy = torch.empty(S, dtype=torch.float64, device="cuda")
+    cube_stats = torch.empty(3, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    pairs_per_step = S * P
+    # whole-job units per step and rank: a split cube is one cube over all ranks
+    pairs_per_step = (S_cube * P / ws) if split else S * P
+
+    def detect():
+        if split:
+            nlos.reduce(tau, S, B, energy, cube_stats)
+            shard.combine_cube_stats(cube_stats, dist)
+            nlos.noise_part(scene, tau, counts, cube_stats, S_cube * B)
+        else:
+            nlos.detect(scene, tau, counts, energy)
 
     def step():
         nlos.scene_set_points(scene, pts_dev)
         nlos.forward(scene, tau)
-        nlos.detect(scene, tau, counts, energy)
+        detect()
 
     for _ in range(max(3, warmup)):
         step()
@@ -310,7 +333,7 @@ def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=N
         e[1].record(stream)
         nlos.forward(scene, tau)
         e[2].record(stream)
-        nlos.detect(scene, tau, counts, energy)
+        detect()
         e[3].record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -333,7 +356,7 @@ def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=N
     for _ in range(2):
         nlos.scene_set_points(scene, pts_host)
         nlos.forward(scene, tau)
-        nlos.detect(scene, tau, counts, energy)
+        detect()
         counts_host.copy_(counts, non_blocking=True)
     torch.cuda.synchronize()
     for k in range(steps):
@@ -342,7 +365,7 @@ def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=N
         a.record(stream)
         nlos.scene_set_points(scene, pts_host)          # H2D of the step's points
         nlos.forward(scene, tau)
-        nlos.detect(scene, tau, counts, energy)
+        detect()
         counts_host.copy_(counts, non_blocking=True)    # D2H of the step's result
         b.record(stream)
     torch.cuda.synchronize()
@@ -353,8 +376,8 @@ def measure_workload(name, rank, steps, warmup, local, dist, ws, peaks, clocks=N
 
     props = torch.cuda.get_device_properties(local)
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    st = nlos.simulate(scene, tau, counts, energy, stats=True)
-    roof = forward_roofline(name, float(fwd_ms.mean()) * 1e-3, st, pairs_per_step,
+    st = nlos.simulate(scene, tau, None, None, stats=True)
+    roof = forward_roofline(name, float(fwd_ms.mean()) * 1e-3, st, S * P,
                             props.multi_processor_count, sm_max, peaks, S, B)
     scene.destroy()
     return {"value": value, "ms_per_step": t_total * 1e3 / steps,
@@ -379,23 +402,27 @@ def run_ours(args):
     nlos.load()
     peaks = device_peaks()
 
+    split = ws > 1 and not args.replicas
     head = measure_workload(HEADLINE, rank, args.steps, args.warmup, local, dist, ws, peaks,
-                            clocks=ClockSampler(local))
+                            clocks=ClockSampler(local), split=split)
     extra = None
     if args.union_steps > 0:
         extra = measure_workload("union64", rank, args.union_steps, args.warmup, local, dist, ws,
-                                 peaks)
+                                 peaks, split=split)
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong" if split else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict({"workload": WORKLOAD_DESC[HEADLINE]}, **head["shape"],
                            l2="flushed by a 256 MB write between timed steps (outside the step "
                               "events)",
                            step="scene_set_points (ingest: spatial order + pack + bounds) + "
                                 "forward (pair histogram + fused jitter) + detect (FP64 energy, "
                                 "cube max and sums, Poisson noise)",
-                           parallelism=f"{ws} independent scenes, one per GPU"),
+                           parallelism=(f"one cube split over {ws} GPUs by scan rows (all "
+                                        f"points on every GPU; one all-reduce of the cube "
+                                        f"statistics before the noise)") if split else
+                           f"{ws} independent scenes, one per GPU"),
             "transients_per_s": head["transients_per_s"], "wall_s": head["wall_s"],
             "clocks": head["clocks"], "gpu_launches": 8 * args.steps,
             "phase_ms": head["phase_ms"], "roofline": head["roofline"], "e2e": head["e2e"]}
@@ -412,6 +439,10 @@ def run_ours(args):
         line["splat_adjoint"] = splat_adjoint_bench(args.splat_steps, 1, peaks)
     if rank == 0 and ws == 1 and args.serving_requests > 0:
         line["serving"] = serving_bench(args.serving_requests, args.serving_rate)
+    if rank == 0 and ws == 1 and args.saturate_requests > 0:
+        # the same request mix arriving far faster than either mode serves it
+        # (a saturating leg: throughput at full load, latency dominated by queueing)
+        line["serving_saturated"] = serving_bench(args.saturate_requests, args.saturate_rate)
     if rank == 0 and ws == 1 and args.lct_steps > 0:
         line["lct"] = lct_bench(args.lct_steps)
     if rank == 0 and ws == 1 and args.occlusion_steps > 0:
@@ -641,6 +672,24 @@ def splat_adjoint_bench(steps: int, warmup: int, peaks=None):
     return out
 
 
+_POOLS = {}
+
+
+def _serving_pools():
+    """Point pools of the serving replays: one union scene and one heightfield
+    of ~2M points; a request with P points takes the first P pool points (a
+    view: no copy per request, so thousands of requests hold no more host
+    memory than the pools; patch areas as in the pool)."""
+    if not _POOLS:
+        import scenes
+        rng = np.random.default_rng(scenes.SEED_BASE + 55)
+        pool_u, _ = scenes.primitive_union_points(rng, 2_000_000)
+        pool_h = scenes.heightfield_points(rng, 1415)
+        _POOLS["u"] = np.ascontiguousarray(pool_u[rng.permutation(len(pool_u))])
+        _POOLS["h"] = np.ascontiguousarray(pool_h[rng.permutation(len(pool_h))])
+    return _POOLS["u"], _POOLS["h"]
+
+
 def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
     """Replays one seeded Poisson-arrival trace (the serving workload: scan side
     16-256, bins 256-2048, 4-16 ps, 1e4-2e6 points, confocal or not, union or
@@ -654,15 +703,7 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
     from paper_2506_03747_gb300 import nlos
 
     reqs = scenes.serving_trace(n_requests=n_requests, rate_hz=rate_hz)
-    # point pools: one union scene and one heightfield of ~2M points; a request
-    # with P points takes the first P pool points (a view: no copy per request,
-    # so 2000 requests hold no more host memory than the pools; patch areas as
-    # in the pool)
-    rng = np.random.default_rng(scenes.SEED_BASE + 55)
-    pool_u, _ = scenes.primitive_union_points(rng, 2_000_000)
-    pool_h = scenes.heightfield_points(rng, 1415)
-    pool_u = np.ascontiguousarray(pool_u[rng.permutation(len(pool_u))])
-    pool_h = np.ascontiguousarray(pool_h[rng.permutation(len(pool_h))])
+    pool_u, pool_h = _serving_pools()
     pts_of = []
     for r in reqs:
         pool = pool_u if r["kind"] == "union" else pool_h
@@ -773,6 +814,9 @@ def main():
                     help="scan points in the CPU baseline sample")
     ap.add_argument("--ref-scan", type=int, default=256,
                     help="scan points per step of the reference (oracle) arm")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1: every GPU simulates its own scene (weak scaling) instead "
+                         "of one cube split by scan rows (strong scaling)")
     ap.add_argument("--union-steps", type=int, default=10,
                     help="timed steps of the union64 workload reported beside the headline "
                          "(0: skip)")
@@ -786,6 +830,10 @@ def main():
                     help="requests in the serving replay (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=200.0,
                     help="Poisson arrival rate of the serving replay [1/s]")
+    ap.add_argument("--saturate-requests", type=int, default=400,
+                    help="requests in the saturating serving leg (0: skip)")
+    ap.add_argument("--saturate-rate", type=float, default=100000.0,
+                    help="arrival rate of the saturating serving leg [1/s]")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

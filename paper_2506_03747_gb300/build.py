@@ -49,6 +49,9 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    # the library is stamped with the newest input time seen here, so a source
+    # edited while this build runs makes the next build() rebuild
+    t_inputs = max(os.path.getmtime(f) for f in sources() + _deps() + [__file__])
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
@@ -71,6 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    os.utime(LIB, (t_inputs, t_inputs))
     return LIB
 
 

@@ -108,7 +108,7 @@ struct SceneScratch {
   unsigned long long pairs_full;  // pairs through the full evaluation (past the early out)
   unsigned long long next_chunk;  // forward: next chunk of work units to claim
   unsigned long long pairs_tested;  // pairs of the units the forward staged
-  unsigned long long pad3;
+  unsigned long long n_live;      // forward: entries of its live-unit list
 };
 constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
 static_assert(sizeof(SceneScratch) == 80, "scratch layout");

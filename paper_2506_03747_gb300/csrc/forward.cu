@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(1024, 1)
   sm.stage = reinterpret_cast<PointPair*>(smem + hist_bytes);
   sm.bars = reinterpret_cast<uint64_t*>(sm.stage + (size_t)a.stages * a.ppb);
   sm.units = reinterpret_cast<unsigned long long*>(sm.bars + 2 * a.stages);
-  sm.rows = reinterpret_cast<uint32_t*>(sm.units + a.stages + 1);
+  sm.lane_units = sm.units + a.stages + 1;
+  sm.rows = reinterpret_cast<uint32_t*>(sm.lane_units + 32);
   if (threadIdx.x == 0) {
     for (uint32_t i = 0; i < a.stages; ++i) {
       mbar_init(&sm.bars[i], 1);                                 // full
@@ -55,6 +56,49 @@ __global__ void __launch_bounds__(1024, 1)
   // the count is warp-uniform: one lane adds it, 64 pairs per warp iteration
   if ((threadIdx.x & 31) == 0 && cnt.full) atomicAdd(a.pairs_full, cnt.full * 64ull);
   if ((threadIdx.x & 31) == 0 && cnt.tested) atomicAdd(a.pairs_tested, cnt.tested * 64ull);
+}
+
+// The live units of a pass, for the forward's chunk claims: one CTA per
+// (tile, window) tests the point blocks against the bounds (unit_live, as
+// the producer warp would) and appends the live ones, with the histogram rows
+// they can touch, to the list (unit | rows << 32). Entries of one (tile,
+// window) are contiguous, so a chunk of the list rarely spans two tiles; the
+// order of the (tile, window) runs in the list does not matter.
+template <int SCAN, int COS, int MODE>
+__global__ void __launch_bounds__(256) unit_list_kernel(const __grid_constant__ FwdArgs a,
+                                                        int mom_J,
+                                                        unsigned long long* __restrict__ list,
+                                                        unsigned long long* __restrict__ n_live) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ unsigned long long s_base;
+  const unsigned long long tw = blockIdx.x;
+  const float margin = window_margin<MODE>(a, mom_J);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t b0 = 0; b0 < a.n_blk; b0 += blockDim.x) {
+    const uint32_t blk = b0 + threadIdx.x;
+    const unsigned long long unit = tw * a.n_blk + blk;
+    float ulo = 0.f, uhi = 0.f;
+    const bool live = blk < a.n_blk && unit_live<SCAN, COS>(a, unit, margin, ulo, uhi);
+    const uint32_t rows = live ? unit_rows(ulo, uhi, margin, a.bw) : 0u;
+    const uint32_t m = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const uint32_t c = s_warp[w];
+        s_warp[w] = tot;
+        tot += c;
+      }
+      s_base = tot ? atomicAdd(n_live, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (live) {
+      const uint32_t pos = s_warp[warp] + __popc(m & ((1u << lane) - 1u));
+      list[s_base + pos] = unit | ((unsigned long long)rows << 32);
+    }
+    __syncthreads();
+  }
 }
 
 // Per-pair table (debug/parity): the same pack and pair_eval2 arithmetic on
@@ -102,6 +146,29 @@ __global__ void pair_table_kernel(const PairTableArgs t, const ScanPoint* scan, 
 namespace {
 
 using FwdFn = void (*)(FwdArgs, MomTab, OccSet);
+using ListFn = void (*)(FwdArgs, int, unsigned long long*, unsigned long long*);
+
+template <int SCAN, int COS>
+ListFn pick_list_mode(int mode) {
+  switch (mode) {
+    case MODE_NEAREST: return unit_list_kernel<SCAN, COS, MODE_NEAREST>;
+    case MODE_NEAREST_OCC: return unit_list_kernel<SCAN, COS, MODE_NEAREST_OCC>;
+    case MODE_SPLAT_MOM: return unit_list_kernel<SCAN, COS, MODE_SPLAT_MOM>;
+    case MODE_SPLAT: return unit_list_kernel<SCAN, COS, MODE_SPLAT>;
+    default: return nullptr;  // the boundary count evaluates every unit
+  }
+}
+
+ListFn pick_list(int scan, int cos, int mode) {
+  if (scan == NLOS_CONFOCAL) {
+    if (cos == NLOS_COS_NONE) return pick_list_mode<NLOS_CONFOCAL, NLOS_COS_NONE>(mode);
+    if (cos == NLOS_COS_OBJECT) return pick_list_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT>(mode);
+    return pick_list_mode<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>(mode);
+  }
+  if (cos == NLOS_COS_NONE) return pick_list_mode<NLOS_NONCONFOCAL, NLOS_COS_NONE>(mode);
+  if (cos == NLOS_COS_OBJECT) return pick_list_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>(mode);
+  return pick_list_mode<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>(mode);
+}
 
 template <int SCAN, int COS>
 FwdFn pick_mode(int mode) {
@@ -215,7 +282,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   }
   // staged blocks, then full + empty barriers and the unit number of each slot
   const size_t stage_bytes = a.stages * (size_t)a.ppb * sizeof(PointPair) + 24 * a.stages + 64 +
-                             4 * kRowWords;
+                             8 * 32 + 4 * kRowWords;
   size_t smem;
   if (moments) {
     // window rows plus 2J halo rows fit the kMomRows moment histograms
@@ -261,8 +328,39 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   const unsigned long long per_cta = a.units / (grid * NLOS_FWD_CHUNKS_PER_CTA);
   a.chunk = std::min<unsigned long long>(std::min<unsigned long long>(std::max<unsigned long long>(per_cta, 8), 64),
                                          std::max<unsigned long long>(1, a.units / grid));
+  // With block bounds, a first kernel lists the live units and the forward
+  // claims chunks of that list: a chunk then holds NLOS_FWD_LIST_MIN.. units
+  // that all carry work (mostly of one tile), instead of a fixed run of
+  // units of which most may be culled, so tile changes (flush, zeroing,
+  // barriers) are fewer per unit of work.
+  ListFn lf = (NLOS_FWD_CULL && a.bounds) ? pick_list(g.scan_mode, g.cos_mode, mode) : nullptr;
+  unsigned long long* list = nullptr;
+  if (lf) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&list), sizeof(unsigned long long) * a.units, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&sc.scratch->n_live, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+      lf<<<(unsigned)(a.units / a.n_blk), 256, 0, st>>>(a, moments ? mt.J : 0, list,
+                                                          &sc.scratch->n_live);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      cudaFreeAsync(list, st);
+      return e;
+    }
+    a.unit_list = list;
+    a.n_live = &sc.scratch->n_live;
+    a.list_chunks_per_cta = NLOS_FWD_LIST_CHUNKS_PER_CTA;
+    a.list_min_chunk = NLOS_FWD_LIST_MIN;
+    a.list_max_chunk = NLOS_FWD_LIST_MAX;
+  }
   fn<<<(unsigned)grid, threads, smem, st>>>(a, mt, sc.occ);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (list) {
+    const cudaError_t ef = cudaFreeAsync(list, st);
+    if (e == cudaSuccess) e = ef;
+  }
+  return e;
 }
 
 cudaError_t launch_pair_table(const SceneImpl& sc, uint64_t s_begin, uint64_t s_count, float* u,

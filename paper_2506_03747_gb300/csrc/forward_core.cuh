@@ -53,6 +53,15 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #ifndef NLOS_FWD_CHUNKS_PER_CTA
 #define NLOS_FWD_CHUNKS_PER_CTA 32          // standalone forward: claimed chunks per CTA (mean)
 #endif
+#ifndef NLOS_FWD_LIST_CHUNKS_PER_CTA
+#define NLOS_FWD_LIST_CHUNKS_PER_CTA 6      // live-unit list: chunks per CTA (mean)
+#endif
+#ifndef NLOS_FWD_LIST_MIN
+#define NLOS_FWD_LIST_MIN 2                 // live-unit list: entries per chunk, at least
+#endif
+#ifndef NLOS_FWD_LIST_MAX
+#define NLOS_FWD_LIST_MAX 64                // ... and at most
+#endif
 #ifndef NLOS_FWD_STAGES
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
 #endif
@@ -111,6 +120,13 @@ struct FwdArgs {
   unsigned long long* next_chunk;  // standalone launch: chunk counter (zeroed per pass)
   unsigned long long units;   // standalone launch: total units
   unsigned long long chunk;   // standalone launch: units per claimed chunk
+  // standalone launch with a unit list (unit_list_kernel): the live units, as
+  // unit | rows << 32 (rows: unit_rows), *n_live of them; chunks of the list
+  // are claimed instead of chunks of units (null: no list)
+  const unsigned long long* unit_list;
+  const unsigned long long* n_live;
+  uint32_t list_chunks_per_cta;  // list chunks per CTA (mean)
+  uint32_t list_min_chunk, list_max_chunk;  // list entries per chunk, clamped
   uint32_t n_pairs, S, B, bw, n_win, n_blk, ppb;
   uint32_t stages;   // staged point blocks (standalone warp-specialised kernel)
   float kbin;        // bins per metre of the scanned leg
@@ -301,6 +317,7 @@ struct FwdSmem {
   uint64_t* bars;              // full[stages] then empty[stages] (initialised by the caller)
   unsigned long long* units;   // [stages]: the unit staged in each slot
   uint32_t* rows = nullptr;    // [kRowWords] or null: row tracking (see fwd_run_ws)
+  unsigned long long* lane_units = nullptr;  // [32]: the producer lanes' units (list mode)
 };
 // rows: 32 words for the producer's lanes, then one per slot (up to 8 stages)
 constexpr int kMaxRangedStages = 8;
@@ -918,6 +935,15 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     // against the bounds (unit_live), then lane 0 stages the live ones in
     // order. Chunk claims (lane 0) run one ahead of their use.
     const float margin = window_margin<MODE>(a, mom_J);
+    // list mode: chunks of the live-unit list, sized from its length
+    const bool listed = a.unit_list != nullptr && chunk_counter != nullptr &&
+                        sm.lane_units != nullptr;
+    if (listed) {
+      units_total = *reinterpret_cast<const volatile unsigned long long*>(a.n_live);
+      chunk = units_total / ((unsigned long long)gridDim.x * a.list_chunks_per_cta);
+      chunk = min(max(chunk, (unsigned long long)a.list_min_chunk),
+                  (unsigned long long)a.list_max_chunk);
+    }
     unsigned long long cur = u0, lim = u1, next = 0;
     bool have_next = false;  // a chunk claimed ahead of its use
     uint32_t claims = 0;
@@ -952,11 +978,21 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
       }
       if (cur >= lim) break;
       const uint32_t n = (uint32_t)min(32ull, lim - cur);
-      float ulo = 0.f, uhi = 0.f;
-      const bool live = lane < n && (!cull || unit_live<SCAN, COS>(a, cur + lane, margin, ulo, uhi));
-      if (ranged) {
-        s_lane_rows[lane] = live ? unit_rows(ulo, uhi, margin, a.bw) : 0u;
+      bool live;
+      if (listed) {
+        // every list entry is live; its rows were found with it
+        live = lane < n;
+        const unsigned long long e = live ? a.unit_list[cur + lane] : 0ull;
+        sm.lane_units[lane] = e & 0xFFFFFFFFull;
+        if (ranged) s_lane_rows[lane] = (uint32_t)(e >> 32);
         __syncwarp();
+      } else {
+        float ulo = 0.f, uhi = 0.f;
+        live = lane < n && (!cull || unit_live<SCAN, COS>(a, cur + lane, margin, ulo, uhi));
+        if (ranged) {
+          s_lane_rows[lane] = live ? unit_rows(ulo, uhi, margin, a.bw) : 0u;
+          __syncwarp();
+        }
       }
       uint32_t mask = __ballot_sync(0xffffffffu, live);
       if (lane == 0) {
@@ -972,11 +1008,12 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
             failed = true;
             break;
           }
-          unsigned long long tag = cur + j;
+          const unsigned long long unit = listed ? sm.lane_units[j] : cur + j;
+          unsigned long long tag = unit;
           if (MODE == MODE_NEAREST_OCC)
-            tag |= (unsigned long long)occ_unit_mask(a, cur + j, *occ) << kUnitBits;
+            tag |= (unsigned long long)occ_unit_mask(a, unit, *occ) << kUnitBits;
           if (ranged) {
-            const long long utw = (long long)((cur + j) / a.n_blk);
+            const long long utw = (long long)(unit / a.n_blk);
             const uint32_t ur = s_lane_rows[j];
             if (utw != run_tw) {
               run_tw = utw;
@@ -989,7 +1026,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
           }
           unit_of[slot] = tag;
           fence_proxy_async_smem();
-          issue_block(a, sm, cur + j, slot);
+          issue_block(a, sm, unit, slot);
           ++k;
         }
       }

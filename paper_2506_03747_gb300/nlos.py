@@ -113,6 +113,9 @@ def load(path: str | None = None):
             "nlos_scene_create": (S, [ctypes.POINTER(Params), _P, _U64, ctypes.c_int, _P,
                                       ctypes.POINTER(ctypes.c_void_p)]),
             "nlos_scene_destroy": (S, [_P]),
+            "nlos_scene_create_rows": (S, [ctypes.POINTER(Params), _P, _U64, ctypes.c_int, _U32,
+                                           _U32, _P, ctypes.POINTER(ctypes.c_void_p)]),
+            "nlos_noise_part": (S, [_P, _P, _P, _P, _U64, _P]),
             "nlos_scene_shape": (S, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U32),
                                      ctypes.POINTER(_U64)]),
             "nlos_simulate": (S, [_P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
@@ -269,6 +272,37 @@ def scene_create(prm, points, stream=None) -> Scene:
     S, B, P = _U64(), _U32(), _U64()
     _check(lib.nlos_scene_shape(h, ctypes.byref(S), ctypes.byref(B), ctypes.byref(P)))
     return Scene(h.value, S.value, B.value, P.value, prm)
+
+
+def scene_create_rows(prm, points, row_begin: int, row_count: int, stream=None) -> Scene:
+    """A scene for scan rows [row_begin, row_begin + row_count) of the grid of
+    ``prm`` (a part of a cube split by rows); points as in scene_create."""
+    lib = load()
+    if isinstance(prm, dict):
+        prm = params(prm)
+    on_dev = 0
+    if hasattr(points, "is_cuda"):
+        on_dev = int(points.is_cuda)
+        if points.dtype.__str__() != "torch.float32" or not points.is_contiguous():
+            raise ValueError("points must be a contiguous float32 tensor")
+        n = points.shape[0] if points.numel() else 0
+    else:
+        points = np.ascontiguousarray(points, dtype=np.float32)
+        n = points.shape[0] if points.size else 0
+    h = ctypes.c_void_p()
+    _check(lib.nlos_scene_create_rows(ctypes.byref(prm), _ptr(points) if n else None, n, on_dev,
+                                      int(row_begin), int(row_count), _stream(stream),
+                                      ctypes.byref(h)))
+    S, B, P = _U64(), _U32(), _U64()
+    _check(lib.nlos_scene_shape(h, ctypes.byref(S), ctypes.byref(B), ctypes.byref(P)))
+    return Scene(h.value, S.value, B.value, P.value, prm)
+
+
+def noise_part(scene: Scene, tau, counts, cube_stats, cube_bins: int, stream=None):
+    """Noise of a part with the whole cube's statistics (float64 CUDA tensor
+    [3]: max, sum, sum of squares) over cube_bins bins."""
+    _check(_lib.nlos_noise_part(scene.handle, _ptr(tau), _ptr(counts), _ptr(cube_stats),
+                                int(cube_bins), _stream(stream)))
 
 
 def scene_destroy(scene: Scene):
