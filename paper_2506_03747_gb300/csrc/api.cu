@@ -345,16 +345,9 @@ nlos_status nlos_reduce(const float* tau_dev, uint64_t num_traces, uint32_t num_
   }
   NLOS_CUDA_TRY(launch_reduce(tau_dev, num_traces, num_bins, energy_dev, scratch, st));
   if (stats_dev) {
-    // {max, sum, sumsq} as doubles
-    SceneScratch h{};
-    NLOS_CUDA_TRY(cudaMemcpyAsync(&h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
-    NLOS_CUDA_TRY(cudaStreamSynchronize(st));
-    float peak;
-    std::memcpy(&peak, &h.peak_bits, sizeof(peak));
-    double out[3] = {peak, h.sum, h.sumsq};
-    NLOS_CUDA_TRY(cudaMemcpyAsync(stats_dev, out, sizeof(out), cudaMemcpyHostToDevice, st));
+    // {max, sum, sumsq} as doubles, stream-ordered (no host round trip)
+    NLOS_CUDA_TRY(launch_stats_out(scratch, stats_dev, st));
     NLOS_CUDA_TRY(cudaFreeAsync(scratch, st));
-    NLOS_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return NLOS_OK;
 }

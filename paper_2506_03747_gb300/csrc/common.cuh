@@ -109,9 +109,10 @@ struct SceneScratch {
   unsigned long long next_chunk;  // forward: next chunk of work units to claim
   unsigned long long pairs_tested;  // pairs of the units the forward staged
   unsigned long long n_live;      // forward: entries of its live-unit list
+  unsigned long long noise_next;  // noise: next chunk of bins to claim
 };
 constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
-static_assert(sizeof(SceneScratch) == 80, "scratch layout");
+static_assert(sizeof(SceneScratch) == 88, "scratch layout");
 
 struct Geometry {
   // host-side resolved parameters; a scene may hold scan rows [row0, row0 + ny)
@@ -146,6 +147,8 @@ cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t
 void jitter_tails(const float* taps, int R, float* tail);
 cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double* energy,
                           SceneScratch* scratch, cudaStream_t st);
+// {max, sum, sum of squares} of a reduction's scratch as three doubles.
+cudaError_t launch_stats_out(const SceneScratch* scratch, double* stats, cudaStream_t st);
 cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,
                          uint32_t stream_tag, uint64_t index_base, uint32_t* counts,
                          cudaStream_t st);

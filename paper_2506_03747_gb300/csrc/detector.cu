@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "device_util.cuh"
 #include "noise_core.cuh"
+#include "reduce_core.cuh"
 
 #include <cmath>
 
@@ -107,7 +108,8 @@ cudaError_t launch_jitter(const float* in, float* out, uint64_t traces, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Reductions: one warp per transient. energy[t] = sum_b tau[t][b] in FP64;
+// Reductions: one warp per transient. energy[t] = sum_b tau[t][b] to FP64
+// accuracy (trace_sums, reduce_core.cuh: error-free FP32 pair sums per lane);
 // the cube's maximum, FP64 sum and sum of squares are combined per CTA in
 // shared memory, then one atomicMax on the float bits (tau >= 0 orders like
 // its bits) and two double atomicAdds per CTA (per-warp atomics on the same
@@ -127,31 +129,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const float* __r
   float cmax = 0.0f;
   for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < traces;
        t += warps) {
-    const float* row = tau + t * B;
-    double s = 0.0, q = 0.0;
-    float m = 0.0f;
-    if ((B & 3u) == 0u) {
-      const float4* r4 = reinterpret_cast<const float4*>(row);
-      for (uint32_t i = lane; i < B / 4; i += 32) {
-        const float4 v = __ldg(r4 + i);
-        s += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
-        q += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
-        m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-      }
-    } else {
-      for (uint32_t i = lane; i < B; i += 32) {
-        const float v = __ldg(row + i);
-        s += (double)v;
-        q += (double)v * v;
-        m = fmaxf(m, v);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      q += __shfl_xor_sync(0xffffffffu, q, o);
-      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
+    double s, q;
+    float m;
+    trace_sums(tau + t * B, B, lane, s, q, m);
     if (lane == 0 && energy) energy[t] = s;
     csum += s;
     csq += q;
@@ -175,6 +155,17 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const float* __r
     atomicAdd(&scratch->sum, csum);
     atomicAdd(&scratch->sumsq, csq);
   }
+}
+
+__global__ void stats_out_kernel(const SceneScratch* scratch, double* stats) {
+  stats[0] = (double)__uint_as_float(scratch->peak_bits);
+  stats[1] = scratch->sum;
+  stats[2] = scratch->sumsq;
+}
+
+cudaError_t launch_stats_out(const SceneScratch* scratch, double* stats, cudaStream_t st) {
+  stats_out_kernel<<<1, 1, 0, st>>>(scratch, stats);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const float* tau, uint64_t traces, uint32_t B, double* energy,
@@ -202,14 +193,20 @@ struct NoiseArgs {
   float peak_photons, dark_cfg, nr_db;
   const double* cube_stats;   // part of a larger cube: {max, sum, sumsq} of the whole
   uint64_t cube_bins;         // bins of the whole cube
+  unsigned long long* next;   // chunk counter, zero at launch
 };
 
 // One resident wave (kNoiseBlocksPerSm CTAs of 256 threads per SM, register
-// budget set by the launch bounds) walks the bins with a grid stride; each
-// thread loads its next bin's tau before sampling the current one, so the
-// HBM latency overlaps the Philox rounds.
+// budget set by the launch bounds). Each warp claims chunks of kNoiseChunk
+// consecutive bins from a counter until none are left (a bin's cost grows
+// with its lambda, and the bright bins of a cube sit at a few time indices:
+// with a fixed grid stride that is a multiple of the bin count, as a resident
+// wave's usually is, some threads got every bright bin); lanes take
+// consecutive bins (coalesced), each loading its next bin's tau before
+// sampling the current one.
 constexpr int kNoiseThreads = 256;
 constexpr int kNoiseBlocksPerSm = 8;
+constexpr uint32_t kNoiseChunk = 128;
 
 __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
   float scale = a.scale, dark = a.dark;
@@ -229,30 +226,53 @@ __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel
       a.scratch->dark = dark;
     }
   }
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  float t = __ldg(a.tau + i);
+  const uint32_t lane = threadIdx.x & 31;
   for (;;) {
-    const uint64_t next = i + stride;
-    const float t_next = next < a.n ? __ldg(a.tau + next) : 0.0f;
-    a.counts[i] = poisson_sample(fmaf(scale, t, dark), a.index_base + i, a.seed, a.tag);
-    if (next >= a.n) break;
-    i = next;
-    t = t_next;
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(a.next, 1ull);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    const uint64_t b0 = c * kNoiseChunk;
+    if (b0 >= a.n) break;
+    const uint64_t b1 = min(a.n, b0 + kNoiseChunk);
+    uint64_t i = b0 + lane;
+    float t = i < b1 ? __ldg(a.tau + i) : 0.0f;
+    for (; i < b1; i += 32) {
+      const uint64_t nx = i + 32;
+      const float t_next = nx < b1 ? __ldg(a.tau + nx) : 0.0f;
+      a.counts[i] = poisson_sample(fmaf(scale, t, dark), a.index_base + i, a.seed, a.tag);
+      t = t_next;
+    }
   }
 }
 
-cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
+// counter: a zeroed word of device memory for the chunk claims, or null (then
+// a stream-ordered one is allocated for this launch).
+cudaError_t launch_noise_impl(NoiseArgs a, cudaStream_t st, unsigned long long* counter) {
   if (a.n == 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = (a.n + kNoiseThreads - 1) / kNoiseThreads;
+  const uint64_t want = (a.n + kNoiseChunk - 1) / kNoiseChunk * 32 / kNoiseThreads + 1;
   const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm;
   const unsigned blocks = (unsigned)(want < wave ? want : wave);
-  noise_kernel<<<blocks, kNoiseThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  unsigned long long* own = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!counter) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&own), sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    counter = own;
+  }
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    a.next = counter;
+    noise_kernel<<<blocks, kNoiseThreads, 0, st>>>(a);
+    e = cudaGetLastError();
+  }
+  if (own) {
+    const cudaError_t ef = cudaFreeAsync(own, st);
+    if (e == cudaSuccess) e = ef;
+  }
+  return e;
 }
 
 cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,
@@ -267,7 +287,7 @@ cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, 
   a.scale = scale;
   a.dark = dark;
   a.scratch = nullptr;
-  return launch_noise_impl(a, st);
+  return launch_noise_impl(a, st, nullptr);
 }
 
 cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scratch, int mode,
@@ -289,7 +309,7 @@ cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scrat
   a.peak_photons = peak_photons;
   a.dark_cfg = dark;
   a.nr_db = nr_db;
-  return launch_noise_impl(a, st);
+  return launch_noise_impl(a, st, scratch ? &scratch->noise_next : nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -62,6 +62,9 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #ifndef NLOS_FWD_LIST_MAX
 #define NLOS_FWD_LIST_MAX 64                // ... and at most
 #endif
+#ifndef NLOS_FWD_CONTIG
+#define NLOS_FWD_CONTIG 1                   // each warp takes a contiguous run of a block's pairs
+#endif
 #ifndef NLOS_FWD_STAGES
 #define NLOS_FWD_STAGES 3                   // staged blocks in flight (warp-specialised)
 #endif
@@ -583,18 +586,28 @@ __device__ __forceinline__ void compute_block(const FwdArgs& a, const PointPair*
                                               int warp_rel, int n_warps, const TileState& ts,
                                               uint32_t col_addr, FwdCount& cnt,
                                               int mom_J = 0, const OccSet* occ = nullptr,
-                                              uint32_t occ_mask = 0) {
+                                              uint32_t occ_mask = 0, uint32_t rot = 0) {
   const float2 kbin2 = make_float2(a.kbin, a.kbin);
   const float2 magic2 = make_float2(kMagic, kMagic);
   const float2 ikbin_neg = make_float2(-1.0f / a.kbin, -1.0f / a.kbin);
+#if NLOS_FWD_CONTIG
+  // a contiguous run of pairs per warp: neighbouring points, so the warps'
+  // shared reductions meet different histogram rows at any one time; the
+  // short last run rotates over the warps from block to block (rot)
+  const uint32_t per = (n + (uint32_t)n_warps - 1u) / (uint32_t)n_warps;
+  const uint32_t run = ((uint32_t)warp_rel + rot) % (uint32_t)n_warps;
+  const uint32_t i_begin = min(n, run * per), i_end = min(n, i_begin + per), i_step = 1u;
+#else
+  const uint32_t i_begin = (uint32_t)warp_rel, i_end = n, i_step = (uint32_t)n_warps;
+#endif
   // iterations of this warp (counted once per block, not per iteration)
-  const uint32_t n_it = n > (uint32_t)warp_rel ? (n - 1u - (uint32_t)warp_rel) / (uint32_t)n_warps + 1u : 0u;
+  const uint32_t n_it = i_end > i_begin ? (i_end - 1u - i_begin) / i_step + 1u : 0u;
   cnt.tested += n_it;
 #if !NLOS_FWD_EARLY
   cnt.full += n_it;
 #endif
 #pragma unroll UNROLL
-  for (uint32_t i = warp_rel; i < n; i += n_warps) {
+  for (uint32_t i = i_begin; i < i_end; i += i_step) {
     PointPair q;
     load_pair(blkp + i, q);
     float2 r2, cn;
@@ -1099,7 +1112,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         const uint32_t first = blk * a.ppb;
         compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb,
                                        min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
-                                       cnt, mom_J, occ, (uint32_t)(tag >> kUnitBits));
+                                       cnt, mom_J, occ, (uint32_t)(tag >> kUnitBits), g);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);

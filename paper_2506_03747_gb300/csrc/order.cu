@@ -52,7 +52,8 @@ __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* curso
 
 // One CTA of kSubPairs threads per sub-block: thread k packs pair k of the
 // sub-block, and the CTA reduces the bounds of its 2 kSubPairs points (the
-// same per-point quantities as block_bound_warp).
+// quantities of block_bound_warp, read off the packed record: the same
+// laser-leg offsets, and liveness from the packed weight factor).
 __global__ void __launch_bounds__(kSubPairs) pack_bounds_kernel(
     const float* __restrict__ raw, uint64_t P, int scan_mode, int cos_mode, double lx, double ly,
     double inv_cdt, const uint32_t* __restrict__ perm, PointPair* pairs, unsigned int* err,
@@ -69,10 +70,24 @@ __global__ void __launch_bounds__(kSubPairs) pack_bounds_kernel(
     hi[c] = -3.0e38f;
   }
   if (k < n_pairs) {
-    pack_pair(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, pairs, err, perm, o);
-    for (uint64_t i = 2 * k; i < min(P, 2 * k + 2); ++i)
-      bound_point(raw + 8 * (perm ? (uint64_t)perm[i] : i), scan_mode, cos_mode, lx, ly, inv_cdt,
-                  lo, hi, live);
+    const PointPair pp = pack_pair_value(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, err,
+                                         perm, o);
+    pairs[k] = pp;
+    // the bounds from the packed record (no second FP64 evaluation): the
+    // laser-leg offset as packed, and "can carry weight" as a nonzero packed
+    // weight factor (zero for albedo or area 0, a point facing away from the
+    // laser, or one hidden from it)
+    for (int h = 0; h < 2 && 2 * k + h < P; ++h) {
+      const float* r = raw + 8 * (perm ? (uint64_t)perm[2 * k + h] : 2 * k + h);
+      const float kq = h ? pp.kq.y : pp.kq.x, na = h ? pp.na.y : pp.na.x;
+      const float nb = h ? pp.nb.y : pp.nb.x, nc = h ? pp.nc.y : pp.nc.x;
+      const float v[7] = {r[0], r[1], r[2], r[3], r[4], r[5], h ? pp.uoff.y : pp.uoff.x};
+      for (int c = 0; c < 7; ++c) {
+        lo[c] = fminf(lo[c], v[c]);
+        hi[c] = fmaxf(hi[c], v[c]);
+      }
+      if (kq != 0.f || na != 0.f || nb != 0.f || nc != 0.f) live = 1.f;
+    }
   }
   bound_warp_reduce(lo, hi, live);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -104,7 +104,11 @@ __device__ __forceinline__ void cell_range(const float* __restrict__ raw, uint64
   for (uint64_t i = b + t0; i < e; i += stride) {
     const uint32_t k = cell_of(raw[8 * i], raw[8 * i + 1], raw[8 * i + 2], lo, inv);
     cell[i] = (uint16_t)k;
-    atomicAdd(&counts[k], 1u);
+    // one atomic per distinct cell of the warp: points given in grid or scan
+    // order put a warp's 32 points in one or two cells, whose counter the
+    // lanes would otherwise increment one after the other
+    const unsigned peers = __match_any_sync(__activemask(), k);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[k], (uint32_t)__popc(peers));
   }
 }
 
@@ -159,7 +163,17 @@ __device__ __forceinline__ void scan_cells(uint32_t* counts, uint32_t* wsum) {
 __device__ __forceinline__ void scatter_range(const uint16_t* cell, uint64_t b, uint64_t e,
                                               uint64_t t0, uint64_t stride, uint32_t* cursor,
                                               uint32_t* perm) {
-  for (uint64_t i = b + t0; i < e; i += stride) perm[atomicAdd(&cursor[cell[i]], 1u)] = (uint32_t)i;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t i = b + t0; i < e; i += stride) {
+    const uint32_t k = cell[i];
+    // the lanes of one cell take consecutive slots from one atomic
+    const unsigned peers = __match_any_sync(__activemask(), k);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(&cursor[k], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    perm[base + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
 }
 
 }  // namespace nlos

@@ -79,7 +79,8 @@ __device__ __forceinline__ PointPair pack_pair_value(const float* __restrict__ r
       } else {
         const double vx = x - lx, vy = y - ly, vz = z;
         const double rl = sqrt(vx * vx + vy * vy + vz * vz);
-        const double cl = -(nx * vx + ny * vy + nz * vz) / rl;
+        const double irl = 1.0 / rl;  // one FP64 division (this part's FP64 pipe is slow)
+        const double cl = -(nx * vx + ny * vy + nz * vz) * irl;
         uoff = rl * inv_cdt;
         bool lit = true;
         if (occ) {
@@ -89,9 +90,9 @@ __device__ __forceinline__ PointPair pack_pair_value(const float* __restrict__ r
         }
         if (!lit) {
           // no weight; kq = s = 0 below
-        } else if (cos_mode == NLOS_COS_NONE) kq = q / (rl * rl);
-        else if (cos_mode == NLOS_COS_OBJECT) s = q * (cl > 0 ? cl : 0.0) / (rl * rl);
-        else s = q * (cl > 0 ? cl : 0.0) / (rl * rl) * (z / rl) * z;
+        } else if (cos_mode == NLOS_COS_NONE) kq = q * irl * irl;
+        else if (cos_mode == NLOS_COS_OBJECT) s = q * (cl > 0 ? cl : 0.0) * irl * irl;
+        else s = q * (cl > 0 ? cl : 0.0) * irl * irl * (z * irl) * z;
       }
       f[h][0] = (float)x;
       f[h][1] = (float)y;

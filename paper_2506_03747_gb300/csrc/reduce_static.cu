@@ -20,6 +20,7 @@
 // cleared between calls; calls whose kernels overlap on the GPU (different
 // streams, no ordering) race on the array.
 #include "common.cuh"
+#include "reduce_core.cuh"
 
 #include <mutex>
 
@@ -66,31 +67,9 @@ __global__ void partials_kernel(const float* __restrict__ tau, uint64_t traces, 
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < traces;
        t += warps) {
-    const float* row = tau + t * B;
-    double s = 0.0, q = 0.0;
-    float m = 0.0f;
-    if ((B & 3u) == 0u) {
-      const float4* r4 = reinterpret_cast<const float4*>(row);
-      for (uint32_t i = lane; i < B / 4; i += 32) {
-        const float4 v = __ldg(r4 + i);
-        s += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
-        q += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
-        m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-      }
-    } else {
-      for (uint32_t i = lane; i < B; i += 32) {
-        const float v = __ldg(row + i);
-        s += (double)v;
-        q += (double)v * v;
-        m = fmaxf(m, v);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      q += __shfl_xor_sync(0xffffffffu, q, o);
-      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
+    double s, q;
+    float m;
+    trace_sums(tau + t * B, B, lane, s, q, m);
     if (lane == 0) {
       if (energy) energy[t] = s;
       part[t].sum = s;
