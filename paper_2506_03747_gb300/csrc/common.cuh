@@ -109,10 +109,9 @@ struct SceneScratch {
   unsigned long long next_chunk;  // forward: next chunk of work units to claim
   unsigned long long pairs_tested;  // pairs of the units the forward staged
   unsigned long long n_live;      // forward: entries of its live-unit list
-  unsigned long long noise_next;  // noise: next chunk of bins to claim
 };
 constexpr size_t kScratchResetOffset = 8;  // offsetof(SceneScratch, peak_bits)
-static_assert(sizeof(SceneScratch) == 88, "scratch layout");
+static_assert(sizeof(SceneScratch) == 80, "scratch layout");
 
 struct Geometry {
   // host-side resolved parameters; a scene may hold scan rows [row0, row0 + ny)

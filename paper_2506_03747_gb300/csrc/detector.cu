@@ -193,17 +193,20 @@ struct NoiseArgs {
   float peak_photons, dark_cfg, nr_db;
   const double* cube_stats;   // part of a larger cube: {max, sum, sumsq} of the whole
   uint64_t cube_bins;         // bins of the whole cube
-  unsigned long long* next;   // chunk counter, zero at launch
+  uint64_t n_chunks;          // chunks of kNoiseChunk bins
+  uint64_t perm;              // chunk permutation: c -> c * perm mod n_chunks (coprime)
 };
 
 // One resident wave (kNoiseBlocksPerSm CTAs of 256 threads per SM, register
-// budget set by the launch bounds). Each warp claims chunks of kNoiseChunk
-// consecutive bins from a counter until none are left (a bin's cost grows
-// with its lambda, and the bright bins of a cube sit at a few time indices:
-// with a fixed grid stride that is a multiple of the bin count, as a resident
-// wave's usually is, some threads got every bright bin); lanes take
-// consecutive bins (coalesced), each loading its next bin's tau before
-// sampling the current one.
+// budget set by the launch bounds). The bins are cut into chunks of
+// kNoiseChunk consecutive bins; warp w takes the chunks w, w + W, w + 2W, ...
+// of a fixed permutation of the chunks (multiplication by a number coprime to
+// their count), so every warp gets bins from all over the cube: a bin's cost
+// grows with its lambda and the bright bins sit at a few time indices of a few
+// transients, and a plain grid stride (a multiple of the bin count for a
+// resident wave) gave some threads every bright bin. No atomics: a shared
+// chunk counter serialised its claims in L2. Lanes take consecutive bins of a
+// chunk (coalesced), each loading its next bin's tau before sampling.
 constexpr int kNoiseThreads = 256;
 constexpr int kNoiseBlocksPerSm = 8;
 constexpr uint32_t kNoiseChunk = 128;
@@ -227,12 +230,12 @@ __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel
     }
   }
   const uint32_t lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long c = 0;
-    if (lane == 0) c = atomicAdd(a.next, 1ull);
-    c = __shfl_sync(0xffffffffu, c, 0);
+  const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (uint64_t k = w; k < a.n_chunks; k += n_warps) {
+    // n_chunks < 2^32 and perm < 2^32 (host), so the product fits 64 bits
+    const uint64_t c = (k * a.perm) % a.n_chunks;
     const uint64_t b0 = c * kNoiseChunk;
-    if (b0 >= a.n) break;
     const uint64_t b1 = min(a.n, b0 + kNoiseChunk);
     uint64_t i = b0 + lane;
     float t = i < b1 ? __ldg(a.tau + i) : 0.0f;
@@ -245,34 +248,35 @@ __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel
   }
 }
 
-// counter: a zeroed word of device memory for the chunk claims, or null (then
-// a stream-ordered one is allocated for this launch).
-cudaError_t launch_noise_impl(NoiseArgs a, cudaStream_t st, unsigned long long* counter) {
+uint64_t gcd64(uint64_t a, uint64_t b) {
+  while (b) {
+    const uint64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+cudaError_t launch_noise_impl(NoiseArgs a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = (a.n + kNoiseChunk - 1) / kNoiseChunk * 32 / kNoiseThreads + 1;
+  a.n_chunks = (a.n + kNoiseChunk - 1) / kNoiseChunk;
+  // a multiplier coprime to the chunk count (identity if the count is large)
+  a.perm = 1;
+  if (a.n_chunks < (1ull << 32)) {
+    for (uint64_t p : {2654435761ull, 2246822519ull, 3266489917ull, 668265263ull, 374761393ull})
+      if (gcd64(p, a.n_chunks) == 1) {
+        a.perm = p;
+        break;
+      }
+  }
+  const uint64_t want = (a.n_chunks * 32 + kNoiseThreads - 1) / kNoiseThreads;
   const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm;
   const unsigned blocks = (unsigned)(want < wave ? want : wave);
-  unsigned long long* own = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (!counter) {
-    e = cudaMallocAsync(reinterpret_cast<void**>(&own), sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    counter = own;
-  }
-  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-  if (e == cudaSuccess) {
-    a.next = counter;
-    noise_kernel<<<blocks, kNoiseThreads, 0, st>>>(a);
-    e = cudaGetLastError();
-  }
-  if (own) {
-    const cudaError_t ef = cudaFreeAsync(own, st);
-    if (e == cudaSuccess) e = ef;
-  }
-  return e;
+  noise_kernel<<<blocks, kNoiseThreads, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,
@@ -287,7 +291,7 @@ cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, 
   a.scale = scale;
   a.dark = dark;
   a.scratch = nullptr;
-  return launch_noise_impl(a, st, nullptr);
+  return launch_noise_impl(a, st);
 }
 
 cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scratch, int mode,
@@ -309,7 +313,7 @@ cudaError_t launch_noise_scene(const float* tau, uint64_t n, SceneScratch* scrat
   a.peak_photons = peak_photons;
   a.dark_cfg = dark;
   a.nr_db = nr_db;
-  return launch_noise_impl(a, st, scratch ? &scratch->noise_next : nullptr);
+  return launch_noise_impl(a, st);
 }
 
 // ---------------------------------------------------------------------------
