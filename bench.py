@@ -802,6 +802,34 @@ def serving_bench(n_requests: int, rate_hz: float, budget_gb: float = 120.0):
             "failures": failures[:5]}
 
 
+def run_profile(args):
+    """Runs `warmup` + `steps` bench steps of one workload (ingest + forward +
+    detect), or forward passes only, and nothing else: the program that the
+    ncu captures under profiles/ were taken of."""
+    import torch
+    from paper_2506_03747_gb300 import build as nbuild
+    from paper_2506_03747_gb300 import nlos
+    nbuild.build()
+    params, pts_np = _workload(args.profile, 0)
+    pts = torch.from_numpy(pts_np).cuda()
+    sc = nlos.scene_create(nlos.params(params), pts)
+    S, B = sc.num_scan, sc.num_bins
+    tau = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    cnt = torch.empty((S, B), dtype=torch.int32, device="cuda")
+    en = torch.empty(S, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        if args.profile_forward:
+            nlos.forward(sc, tau)
+        else:
+            nlos.scene_set_points(sc, pts)
+            nlos.forward(sc, tau)
+            nlos.detect(sc, tau, cnt, en)
+    torch.cuda.synchronize()
+    nlos.scene_check(sc)
+    sc.destroy()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -834,7 +862,13 @@ def main():
                     help="requests in the saturating serving leg (0: skip)")
     ap.add_argument("--saturate-rate", type=float, default=100000.0,
                     help="arrival rate of the saturating serving leg [1/s]")
+    ap.add_argument("--profile", choices=["heightfield128", "union64"], default=None,
+                    help="only run warmup + steps bench steps of this workload (for ncu)")
+    ap.add_argument("--profile-forward", action="store_true",
+                    help="with --profile: forward passes only")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
