@@ -42,20 +42,44 @@ static __device__ __align__(256) TracePartial g_partials[kStaticMaxTraces];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 TracePartial* g_dev_ptr[kMaxDevices] = {};
+void* g_dev_ctx[kMaxDevices] = {};  // the context each address was looked up in
+
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent,
+// found through the runtime so that the library needs no link to the driver
+// library), or null if none is current or the call is unavailable.
+void* current_context() {
+  using CtxGetCurrent = int (*)(void**);
+  static CtxGetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<CtxGetCurrent>(nullptr);
+    return reinterpret_cast<CtxGetCurrent>(f);
+  }();
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
 
 // Device address of g_partials on the current device, looked up once per
-// device (host code must not use the symbol itself as an address).
+// device and context (host code must not use the symbol itself as an
+// address). A context destroyed and made anew (cudaDeviceReset) loads the
+// module again, so an address is reused only in the context it came from.
 cudaError_t partials_address(TracePartial** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_dev_ptr[dev]) {
+  void* ctx = current_context();
+  if (!g_dev_ptr[dev] || !ctx || ctx != g_dev_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_partials);
+    e = cudaGetSymbolAddress(&p, g_partials);  // makes the device's context current
     if (e != cudaSuccess) return e;
     g_dev_ptr[dev] = static_cast<TracePartial*>(p);
+    g_dev_ctx[dev] = ctx ? ctx : current_context();
   }
   *out = g_dev_ptr[dev];
   return cudaSuccess;

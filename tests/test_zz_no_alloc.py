@@ -63,3 +63,25 @@ def test_reduce_static_rejects_more_transients_than_its_array():
     with pytest.raises(nlos.NlosError) as ei:
         nlos.reduce_static(t, 65537, 4, None, None)
     assert ei.value.status == nlos.EINVAL
+
+
+def test_reduce_static_optional_outputs_and_empty():
+    """Either output may be omitted, and zero transients is a valid call (the
+    statistics of an empty cube are zeros)."""
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(7)
+    x = (rng.random((300, 256)) ** 3).astype(np.float32)
+    t = torch.from_numpy(x).cuda()
+    e_ref, s_ref = _ref(t, 300, 256)
+    en = torch.full((300,), -1.0, dtype=torch.float64, device="cuda")
+    nlos.reduce_static(t, 300, 256, en, None)
+    st = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    nlos.reduce_static(t, 300, 256, None, st)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(en.cpu().numpy(), e_ref, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(st.cpu().numpy(), s_ref, rtol=1e-12, atol=0)
+    st0 = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    nlos.reduce_static(t, 0, 256, None, st0)
+    torch.cuda.synchronize()
+    assert (st0.cpu().numpy() == 0.0).all()
