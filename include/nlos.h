@@ -306,21 +306,32 @@ nlos_status nlos_reduce(const float* tau_dev, uint64_t num_traces, uint32_t num_
  * results are kept in a fixed 1.5 MiB array in the library's device image,
  * which every device that loads the library holds until the process exits.
  * The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream
- * capture. Every call reuses the array: calls whose work may overlap on the
+ * device, with the device current, and again only if the device's context
+ * was destroyed and made anew, e.g. after cudaDeviceReset); make that first
+ * call before any stream capture. Every call reuses the array: calls whose work may overlap on the
  * GPU (unordered streams) race on it and must be serialised by the caller. */
 nlos_status nlos_reduce_static(const float* tau_dev, uint64_t num_traces, uint32_t num_bins,
                                double* energy_dev, double* stats_dev, void* cuda_stream);
 
-/* Poisson noise: counts[i] ~ Poisson(fmaf(scale, tau[i], dark)) drawn from
- * the Philox4x32-10 stream of global bin index index_base + i: key =
- * (seed_lo, seed_hi), counter = (index_lo, index_hi, block, stream_tag),
- * uniforms ((word >> 9) + 0.5) * 2^-23. Three exact samplers by range:
- * lambda < 30, Knuth's multiplication method (single-precision products
- * against expf(-lambda)); 30 <= lambda < 150, the sum of ceil(lambda / 30)
- * Knuth draws of mean lambda / ceil(lambda / 30), one after the other from the
- * same stream (a sum of independent Poisson variables is Poisson);
- * lambda >= 150, Hoermann's PTRS (1993) in double precision. */
+/* Poisson noise (Eq. 18/19): counts[i] ~ Poisson(fmaf(scale, tau[i], dark))
+ * for the global bin index j = index_base + i. Draws: key = (seed_lo,
+ * seed_hi); bins go in groups of four, and the first uniform of bin j is word
+ * (j mod 4) of the Philox4x32-10 block at counter (g_lo, g_hi, 0, stream_tag),
+ * g = j / 4; any further uniform comes from the bin's own counters
+ * (j_lo, j_hi, 1 + b, stream_tag), b = 0, 1, ..., word after word; a word w
+ * gives the uniform ((w >> 9) + 0.5) * 2^-23. Three exact samplers by range:
+ * lambda < 30, inversion by sequential search from the first uniform in
+ * single precision (p_0 = expf(-lambda), p_k = (p_{k-1} lambda) (1/k),
+ * F_k = F_{k-1} + p_k; the first k with u <= F_k, or the first k whose term
+ * leaves F unchanged); 30 <= lambda < 150, the sum of ceil(lambda / 30) such
+ * draws of mean lambda / ceil(lambda / 30), the first from the first uniform
+ * and the others from the own counters (a sum of independent Poisson
+ * variables is Poisson); lambda >= 150, Hoermann's PTRS (1993) in double
+ * precision on the own counters. lambda <= 0 or NaN gives 0.
+ * tau_dev, counts_dev: n floats / uint32 on the device (any alignment; 16-byte
+ * alignment with index_base a multiple of 4 takes the vector path).
+ * Asynchronous on cuda_stream; NLOS_EINVAL for null pointers with n > 0 and
+ * for a scale or dark that is not finite and >= 0. */
 nlos_status nlos_noise(const float* tau_dev, uint64_t n, float scale, float dark, uint64_t seed,
                        uint32_t stream_tag, uint64_t index_base, uint32_t* counts_dev,
                        void* cuda_stream);

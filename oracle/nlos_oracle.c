@@ -386,9 +386,13 @@ void orc_philox_many(const uint32_t* ctr, int64_t n, const uint32_t key[2], uint
 }
 
 /* ---------------------------------------------------------------------------
- * Per-bin random stream: key = (seed_lo, seed_hi), counter =
- * (index_lo, index_hi, block, stream_tag), where index is the global bin index
- * and block counts the 4-word blocks this bin has consumed. A word w maps to
+ * Per-bin random draws, key = (seed_lo, seed_hi). Bins are taken in groups of
+ * four, g = floor(index / 4): the first uniform of bin `index` is word
+ * (index mod 4) of the block at counter (g_lo, g_hi, 0, stream_tag); any
+ * further uniform comes from the bin's own stream, counters
+ * (index_lo, index_hi, 1 + j, stream_tag) for j = 0, 1, ..., one word after
+ * the other. The group counters have a zero third word and the own-stream
+ * counters a nonzero one, so no two draws share a counter. A word w maps to
  * the uniform ((w >> 9) + 0.5) * 2^-23, which lies strictly inside (0, 1) and
  * is exact in single precision.
  * ------------------------------------------------------------------------- */
@@ -399,12 +403,23 @@ typedef struct {
   int pos;
 } orc_stream;
 
+static float word_uniform(uint32_t w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
+
+static float first_uniform(uint64_t index, uint64_t seed, uint32_t stream_tag) {
+  const uint64_t g = index >> 2;
+  const uint32_t ctr[4] = {(uint32_t)g, (uint32_t)(g >> 32), 0u, stream_tag};
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  return word_uniform(out[index & 3u]);
+}
+
 static void stream_init(orc_stream* st, uint64_t index, uint64_t seed, uint32_t stream_tag) {
   st->key[0] = (uint32_t)seed;
   st->key[1] = (uint32_t)(seed >> 32);
   st->ctr[0] = (uint32_t)index;
   st->ctr[1] = (uint32_t)(index >> 32);
-  st->ctr[2] = 0u;
+  st->ctr[2] = 1u;
   st->ctr[3] = stream_tag;
   orc_philox4x32_10(st->ctr, st->key, st->buf);
   st->pos = 0;
@@ -416,38 +431,46 @@ static float stream_uniform(orc_stream* st) {
     orc_philox4x32_10(st->ctr, st->key, st->buf);
     st->pos = 0;
   }
-  uint32_t w = st->buf[st->pos++];
-  return ((float)(w >> 9) + 0.5f) * 0x1p-23f;
+  return word_uniform(st->buf[st->pos++]);
 }
 
 /* ---------------------------------------------------------------------------
  * Poisson sampling (Eq. 18/19). The sampled count decides an integer, so the
  * host and the device take each decision in the same precision: lambda is a
  * single-precision value and the uniforms are exact in single precision;
- *  - lambda < 30: Knuth's multiplication method in single precision (multiply
- *    uniforms until the product drops to expf(-lambda) or below; the count is
- *    the number of factors minus one);
- *  - 30 <= lambda < 150: the sum of n = ceil(lambda / 30) Knuth draws of
- *    mean lambda / n (single precision, drawn one after the other from the
- *    same stream); a sum of independent Poisson variables is Poisson with
- *    the summed mean, so this is exact and keeps the device off double
- *    precision for the counts near a 100-photon peak;
+ *  - lambda < 30: inversion by sequential search in single precision, from
+ *    one uniform u: p_0 = expf(-lambda), F_0 = p_0, and for k = 1, 2, ...
+ *    p_k = (p_{k-1} lambda) (1/k), F_k = F_{k-1} + p_k, each product, the
+ *    reciprocal 1/k and the sum rounded to single precision; the count is
+ *    the first k with u <= F_k. The search also stops at the first k whose
+ *    term no longer changes F (the single-precision CDF has stopped moving,
+ *    a tail of probability ~1e-7), and after 1000 steps;
+ *  - 30 <= lambda < 150: the sum of n = ceil(lambda / 30) inversion draws of
+ *    mean lambda / n (the first from the bin's first uniform, the others from
+ *    its own stream); a sum of independent Poisson variables is Poisson with
+ *    the summed mean, so this is exact and keeps every draw in the range
+ *    where expf(-mean) is a normal single-precision number;
  *  - lambda >= 150: PTRS, the transformed rejection method with squeeze of
  *    W. Hoermann, "The transformed rejection method for generating Poisson
  *    random variables", Insurance: Mathematics and Economics 12 (1993),
  *    evaluated in double (log and lgamma of double agree to about the last
- *    bit on host and device, where single-precision lgammaf does not).
- * Both loops are capped at 1000 steps (never reached in practice).
+ *    bit on host and device, where single-precision lgammaf does not), its
+ *    uniforms all from the bin's own stream.
+ * The PTRS loop is capped at 1000 steps (never reached in practice).
  * lambda <= 0 or NaN gives 0.
  * ------------------------------------------------------------------------- */
-static uint32_t poisson_knuth(float lam, orc_stream* st) {
-  float limit = expf(-lam);
-  float prod = 1.0f;
+static uint32_t poisson_inversion(float lam, float u) {
+  float p = expf(-lam);
+  float F = p;
   uint32_t k = 0;
-  for (int it = 0; it < 1000; ++it) {
-    prod *= stream_uniform(st);
-    if (prod <= limit) return k;
-    k += 1;
+  while (u > F && k < 1000u) {
+    k += 1u;
+    const float rk = 1.0f / (float)k;
+    const float q = p * lam;
+    p = q * rk;
+    const float Fn = F + p;
+    if (Fn == F) break;
+    F = Fn;
   }
   return k;
 }
@@ -476,14 +499,14 @@ static uint32_t poisson_ptrs(float lam_f, orc_stream* st) {
 
 uint32_t orc_poisson_one(float lam, uint64_t index, uint64_t seed, uint32_t stream_tag) {
   if (!(lam > 0.0f)) return 0u;
+  if (lam < 30.0f) return poisson_inversion(lam, first_uniform(index, seed, stream_tag));
   orc_stream st;
   stream_init(&st, index, seed, stream_tag);
-  if (lam < 30.0f) return poisson_knuth(lam, &st);
   if (lam < 150.0f) {
     const float parts = ceilf(lam / 30.0f);
     const float sub = lam / parts;
-    uint32_t k = 0;
-    for (int i = 0; i < (int)parts; ++i) k += poisson_knuth(sub, &st);
+    uint32_t k = poisson_inversion(sub, first_uniform(index, seed, stream_tag));
+    for (int i = 1; i < (int)parts; ++i) k += poisson_inversion(sub, stream_uniform(&st));
     return k;
   }
   return poisson_ptrs(lam, &st);

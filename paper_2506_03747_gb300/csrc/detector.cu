@@ -195,21 +195,24 @@ struct NoiseArgs {
   uint64_t cube_bins;         // bins of the whole cube
 };
 
-// One resident wave (kNoiseBlocksPerSm CTAs of 7 warps per SM, 32 registers).
-// Warp w samples the 32 consecutive bins of chunk c = w, w + W, w + 2W, ...
-// (lane = bin, coalesced), each lane loading its next bin's tau before
-// sampling the current one. The warp count W is odd, so the stride W * 32
-// moves a warp's bins through every time index of the transients: a bin's
-// cost grows with its lambda and the bright bins sit at a few time indices,
-// and a stride that is a multiple of the bin count (a wave of 256-thread
-// blocks of 1024-bin transients: 1216 * 256 = 304 * 1024) gave some warps
-// every bright bin of the cube (ncu: SMs 40% active, ALU pipe from 19% to 99%
-// over the SMs). No atomics and no divisions in the loop.
+// One resident wave (kNoiseBlocksPerSm CTAs of 7 warps per SM). A thread
+// samples one group of four bins at a time (one Philox block for the four
+// first draws, a 16-byte load and store); warp w takes the 32 consecutive
+// groups of chunk c = w, w + W, w + 2W, ... (lane = group, coalesced). The
+// warp count W is odd, so the stride W * 128 bins moves a warp's bins through
+// the time indices of the transients: a bin's cost grows with its lambda and
+// the bright bins sit at a few time indices, and a stride that is a multiple
+// of the bin count (a wave of 256-thread blocks of 1024-bin transients:
+// 1216 * 256 = 304 * 1024) gave some warps every bright bin of the cube (ncu:
+// SMs 40% active, ALU pipe from 19% to 99% over the SMs). No atomics and no
+// divisions in the loop; 1/k of the inversion search from a shared table.
 constexpr int kNoiseWarps = 7;
 constexpr int kNoiseThreads = 32 * kNoiseWarps;
-constexpr int kNoiseBlocksPerSm = 9;
+constexpr int kNoiseBlocksPerSm = 8;
 
 __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
+  __shared__ float rcp[kRcpTable];
+  fill_rcp_table(rcp, threadIdx.x, blockDim.x);
   float scale = a.scale, dark = a.dark;
   if (a.cube_stats) {
     scale = noise_scale_of((float)a.cube_stats[0], a.cube_stats[1], a.cube_stats[2], a.mode,
@@ -227,18 +230,12 @@ __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel
       a.scratch->dark = dark;
     }
   }
+  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * kNoiseWarps * 32;
-  uint64_t i = ((uint64_t)blockIdx.x * kNoiseWarps + (threadIdx.x >> 5)) * 32 + (threadIdx.x & 31);
-  if (i >= a.n) return;
-  float t = __ldg(a.tau + i);
-  for (;;) {
-    const uint64_t next = i + stride;
-    const float t_next = next < a.n ? __ldg(a.tau + next) : 0.0f;
-    a.counts[i] = poisson_sample(fmaf(scale, t, dark), a.index_base + i, a.seed, a.tag);
-    if (next >= a.n) break;
-    i = next;
-    t = t_next;
-  }
+  const uint64_t j0 = ((uint64_t)blockIdx.x * kNoiseWarps + (threadIdx.x >> 5)) * 32 +
+                      (threadIdx.x & 31);
+  noise_groups(a.tau, a.counts, 0, a.n, a.index_base, scale, dark, a.seed, a.tag, rcp, j0,
+               stride);
 }
 
 cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
@@ -246,7 +243,8 @@ cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t want = (a.n + kNoiseThreads - 1) / kNoiseThreads;
+  const uint64_t groups = ((a.index_base + a.n + 3) >> 2) - (a.index_base >> 2);
+  const uint64_t want = (groups + kNoiseThreads - 1) / kNoiseThreads;
   const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm;
   uint64_t blocks = want < wave ? want : wave;
   if (blocks > 1 && (blocks & 1u) == 0) --blocks;  // an odd number of warps (7 per block)

@@ -110,7 +110,7 @@ struct PairTableArgs {
   unsigned int* err;
   uint32_t n_pairs, P;
   int scan_mode, cos_mode;
-  double lx, ly, inv_cdt;
+  PackConst pc;
 };
 
 template <int SCAN, int COS>
@@ -122,8 +122,7 @@ __global__ void pair_table_kernel(const PairTableArgs t, const ScanPoint* scan, 
   const uint64_t i = idx / n_pairs;
   const uint32_t k = (uint32_t)(idx % n_pairs);
   const ScanPoint sp = scan[s_begin + i];
-  const PointPair q = pack_pair_value(t.raw, P, k, t.scan_mode, t.cos_mode, t.lx, t.ly, t.inv_cdt,
-                                      t.err, nullptr);
+  const PointPair q = pack_pair_value(t.raw, P, k, t.scan_mode, t.cos_mode, t.pc, t.err, nullptr);
   float2 u, w, cn;
   pair_eval2<SCAN, COS>(q, make_float2(-sp.sx, -sp.sx), make_float2(-sp.sy, -sp.sy),
                         make_float2(sp.off, sp.off), make_float2(kbin, kbin), u, w, cn);
@@ -372,7 +371,7 @@ cudaError_t launch_pair_table(const SceneImpl& sc, uint64_t s_begin, uint64_t s_
   const float kbin = (float)((g.scan_mode == NLOS_CONFOCAL ? 2.0 : 1.0) / g.cdt);
   const unsigned blocks = (unsigned)((total + 255) / 256);
   PairTableArgs t{sc.raw_points, &sc.scratch->err, n_pairs, (uint32_t)g.P, g.scan_mode,
-                  g.cos_mode, sc.params.laser_x, sc.params.laser_y, 1.0 / g.cdt};
+                  g.cos_mode, pack_const(sc.params.laser_x, sc.params.laser_y, 1.0 / g.cdt)};
 #define NLOS_PT(SC, CO) \
   pair_table_kernel<SC, CO><<<blocks, 256, 0, st>>>(t, sc.scan, s_begin, s_count, kbin, u, w)
   if (g.scan_mode == NLOS_CONFOCAL) {

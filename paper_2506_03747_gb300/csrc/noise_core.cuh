@@ -1,6 +1,6 @@
 // Device Poisson noise of the GB300 NLOS simulator (Eq. 18/19 of arXiv
-// 2506.03747, Algorithm 1 step 2.4): per-bin Philox4x32-10 streams and the
-// Knuth / PTRS samplers. Shared by the standalone noise kernel and the
+// 2506.03747, Algorithm 1 step 2.4): Philox4x32-10 draws and the inversion /
+// PTRS samplers. Shared by the standalone noise kernel and the
 // persistent serving kernel.
 #pragma once
 
@@ -12,23 +12,45 @@ namespace nlos {
 // ---------------------------------------------------------------------------
 // Poisson sampling, step for step as the CPU oracle so that both take every
 // integer decision in the same precision: single-precision lambda, uniforms
-// and Knuth threshold, PTRS in double (explicit __d*_rn / __f*_rn intrinsics
+// and inversion sums, PTRS in double (explicit __d*_rn / __f*_rn intrinsics
 // keep the compiler from contracting into FMAs).
-// Per-bin stream: key = (seed_lo, seed_hi), counter = (index_lo, index_hi,
-// block, stream_tag); a word w gives the uniform ((w >> 9) + 0.5) * 2^-23.
-//  * lambda < 30: Knuth's multiplication method against expf(-lambda);
-//  * 30 <= lambda < 150: the sum of ceil(lambda / 30) Knuth draws of mean
-//    lambda / ceil(lambda / 30), one after the other from the same stream
-//    (exact: a sum of independent Poisson variables is Poisson);
+// Draws (key = (seed_lo, seed_hi)): bins go in groups of four, g = index / 4;
+// the first uniform of a bin is word (index mod 4) of the block at counter
+// (g_lo, g_hi, 0, tag), so one Philox block serves four bins' first draws;
+// further uniforms come from the bin's own stream at counters
+// (index_lo, index_hi, 1 + j, tag). A word w gives ((w >> 9) + 0.5) * 2^-23.
+//  * lambda < 30: inversion by sequential search from the first uniform:
+//    p_0 = expf(-lambda), p_k = (p_{k-1} lambda) (1/k), F_k = F_{k-1} + p_k,
+//    count = first k with u <= F_k (or the first k whose term leaves F
+//    unchanged, or 1000);
+//  * 30 <= lambda < 150: the sum of ceil(lambda / 30) inversion draws of mean
+//    lambda / ceil(lambda / 30), the first from the first uniform and the
+//    others from the own stream (exact: a sum of independent Poisson
+//    variables is Poisson);
 //  * lambda >= 150: Hoermann's PTRS (1993), transformed rejection with
-//    squeeze, in double.
+//    squeeze, in double, on the own stream.
 // ---------------------------------------------------------------------------
-// All three are exact; the split only moves work between Knuth's single-
-// precision products (about lambda of them) and the PTRS branch, which runs
-// in FP64 (64 times slower per instruction on this part than FP32).
-constexpr float kKnuthMax = 30.0f;
+// All three are exact; the inversion takes one uniform and about lambda
+// multiply-adds, where Knuth's product method takes about lambda uniforms.
+constexpr float kInvMax = 30.0f;
 constexpr float kSplitMax = 150.0f;
+constexpr int kRcpTable = 64;  // 1/k for k < kRcpTable from a table (shared memory)
 
+__device__ __forceinline__ float word_uniform(uint32_t w) {
+  return __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 0x1p-23f);
+}
+
+// The Philox block of group g (the first draws of bins 4g .. 4g + 3).
+__device__ __forceinline__ uint4 group_block(uint64_t g, uint64_t seed, uint32_t tag) {
+  return philox4x32_10(make_uint4((uint32_t)g, (uint32_t)(g >> 32), 0u, tag), (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ uint32_t group_word(const uint4& b, uint32_t r) {
+  return r == 0 ? b.x : r == 1 ? b.y : r == 2 ? b.z : b.w;
+}
+
+// A bin's own stream (blocks 1, 2, ... of its counter), computed on first use.
 struct BinStream {
   uint4 ctr;
   uint32_t k0, k1;
@@ -38,8 +60,7 @@ struct BinStream {
     ctr = make_uint4((uint32_t)index, (uint32_t)(index >> 32), 0u, tag);
     k0 = (uint32_t)seed;
     k1 = (uint32_t)(seed >> 32);
-    buf = philox4x32_10(ctr, k0, k1);
-    pos = 0;
+    pos = 4;
   }
   __device__ __forceinline__ float uniform() {
     if (pos == 4) {
@@ -49,26 +70,31 @@ struct BinStream {
     }
     const uint32_t w = pos == 0 ? buf.x : pos == 1 ? buf.y : pos == 2 ? buf.z : buf.w;
     ++pos;
-    return __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 0x1p-23f);
+    return word_uniform(w);
   }
 };
 
-__device__ inline uint32_t poisson_knuth(float lam, BinStream& st) {
-  const float limit = expf(-lam);
-  float prod = 1.0f;
+// 1/k rounded to single precision (the correctly rounded reciprocal, as the
+// host's 1.0f / k); rcp: a table of kRcpTable entries or null.
+__device__ __forceinline__ float recip_k(uint32_t k, const float* rcp) {
+  return (rcp && k < (uint32_t)kRcpTable) ? rcp[k] : __frcp_rn((float)k);
+}
+
+__device__ __forceinline__ uint32_t poisson_inversion(float lam, float u, const float* rcp) {
+  float p = expf(-lam);
+  float F = p;
   uint32_t k = 0;
-  for (int it = 0; it < 1000; ++it) {
-    prod = __fmul_rn(prod, st.uniform());
-    if (prod <= limit) return k;
-    k += 1;
+  while (u > F && k < 1000u) {
+    k += 1u;
+    p = __fmul_rn(__fmul_rn(p, lam), recip_k(k, rcp));
+    const float Fn = __fadd_rn(F, p);
+    if (Fn == F) break;
+    F = Fn;
   }
   return k;
 }
 
-// Out of line: the PTRS range is rare (lambda >= 150), and inlined it would
-// set the register budget of every bin's path. The stream is passed by value
-// (it is the bin's last sampler), so it stays in registers on both sides.
-static __device__ __noinline__ uint32_t poisson_ptrs(float lam_f, BinStream st) {
+__device__ __forceinline__ uint32_t poisson_ptrs(float lam_f, BinStream& st) {
   const double lam = (double)lam_f;
   const double slam = sqrt(lam);
   const double loglam = log(lam);
@@ -93,21 +119,96 @@ static __device__ __noinline__ uint32_t poisson_ptrs(float lam_f, BinStream st) 
   return (uint32_t)floor(lam);
 }
 
-__device__ __forceinline__ uint32_t poisson_sample(float lam, uint64_t index, uint64_t seed,
-                                                   uint32_t tag) {
-  if (!(lam > 0.0f)) return 0u;
+// lambda >= 30, out of line: these bins are rare (the bright bins of a
+// cube), and inlined their paths would set the register budget of every bin.
+static __device__ __noinline__ uint32_t poisson_large(float lam, float u0, uint64_t index,
+                                                      uint64_t seed, uint32_t tag,
+                                                      const float* rcp) {
   BinStream st(index, seed, tag);
-  if (lam < kKnuthMax) return poisson_knuth(lam, st);
   if (lam < kSplitMax) {
-    const float parts = ceilf(__fdiv_rn(lam, kKnuthMax));
+    const float parts = ceilf(__fdiv_rn(lam, kInvMax));
     const float sub = __fdiv_rn(lam, parts);
-    uint32_t k = 0;
-    for (int i = 0; i < (int)parts; ++i) k += poisson_knuth(sub, st);
+    uint32_t k = poisson_inversion(sub, u0, rcp);
+    for (int i = 1; i < (int)parts; ++i) k += poisson_inversion(sub, st.uniform(), rcp);
     return k;
   }
   return poisson_ptrs(lam, st);
 }
 
+// The count of bin `index` given its first uniform u0 (from its group block).
+__device__ __forceinline__ uint32_t poisson_from(float lam, float u0, uint64_t index,
+                                                 uint64_t seed, uint32_t tag, const float* rcp) {
+  if (!(lam > 0.0f)) return 0u;
+  if (lam < kInvMax) return poisson_inversion(lam, u0, rcp);
+  return poisson_large(lam, u0, index, seed, tag, rcp);
+}
+
+// One bin on its own (its group block is computed for it alone).
+__device__ __forceinline__ uint32_t poisson_sample(float lam, uint64_t index, uint64_t seed,
+                                                   uint32_t tag, const float* rcp = nullptr) {
+  if (!(lam > 0.0f)) return 0u;
+  const uint4 b = group_block(index >> 2, seed, tag);
+  return poisson_from(lam, word_uniform(group_word(b, (uint32_t)(index & 3u))), index, seed, tag,
+                      rcp);
+}
+
+// Fills a shared table of 1/k (k < kRcpTable; entry 0 unused) with nthreads
+// threads starting at thread t0; the caller synchronises before use.
+__device__ __forceinline__ void fill_rcp_table(float* rcp, int t, int nthreads) {
+  for (int k = t; k < kRcpTable; k += nthreads) rcp[k] = k ? __frcp_rn((float)k) : 0.0f;
+}
+
+// Counts of the bins [b, e) of a cube part (local indices; the global index
+// of local bin l is index_base + l, and lambda = scale * tau + dark), group by
+// group: this thread takes the groups gb + j0, gb + j0 + stride, ... of the
+// groups of four global indices that meet [b, e), computes each group's
+// Philox block once, and samples its (up to four) bins of the range. Interior
+// groups of an aligned part load and store four bins at a time.
+__device__ __forceinline__ void noise_groups(const float* __restrict__ tau,
+                                             uint32_t* __restrict__ counts, uint64_t b, uint64_t e,
+                                             uint64_t index_base, float scale, float dark,
+                                             uint64_t seed, uint32_t tag, const float* rcp,
+                                             uint64_t j0, uint64_t stride) {
+  if (b >= e) return;
+  const uint64_t gb = (index_base + b) >> 2, ge = (index_base + e + 3) >> 2;
+  const bool vec_ok = ((((uintptr_t)tau) | ((uintptr_t)counts)) & 15u) == 0;
+  for (uint64_t g = gb + j0; g < ge; g += stride) {
+    const int64_t l0 = (int64_t)(4 * g) - (int64_t)index_base;  // local index of bin 4g
+    const bool vec = vec_ok && (l0 & 3) == 0 && l0 >= (int64_t)b && l0 + 4 <= (int64_t)e;
+    float t[4];
+    uint32_t in = 0xFu;  // bit r: bin 4g + r lies in the range
+    if (vec) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(tau + l0));
+      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t l = l0 + r;
+        const bool ok = l >= (int64_t)b && l < (int64_t)e;
+        t[r] = ok ? __ldg(tau + l) : 0.0f;
+        if (!ok) in &= ~(1u << r);
+      }
+    }
+    const uint4 blk = group_block(g, seed, tag);
+    uint32_t c[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      // bins outside the range are not sampled
+      const float lam = ((in >> r) & 1u) ? fmaf(scale, t[r], dark) : 0.0f;
+      c[r] = poisson_from(lam, word_uniform(group_word(blk, (uint32_t)r)), 4 * g + r, seed, tag,
+                          rcp);
+    }
+    if (vec) {
+      *reinterpret_cast<uint4*>(counts + l0) = make_uint4(c[0], c[1], c[2], c[3]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t l = l0 + r;
+        if (l >= (int64_t)b && l < (int64_t)e) counts[l] = c[r];
+      }
+    }
+  }
+}
 
 // Noise scale from a cube's reduction results (identical in every thread):
 //  PEAK:     scale = peak_photons / max tau_G (0 for an empty cube);

@@ -55,8 +55,8 @@ __global__ void scatter_kernel(const uint16_t* cell, uint64_t P, uint32_t* curso
 // quantities of block_bound_warp, read off the packed record: the same
 // laser-leg offsets, and liveness from the packed weight factor).
 __global__ void __launch_bounds__(kSubPairs) pack_bounds_kernel(
-    const float* __restrict__ raw, uint64_t P, int scan_mode, int cos_mode, double lx, double ly,
-    double inv_cdt, const uint32_t* __restrict__ perm, PointPair* pairs, unsigned int* err,
+    const float* __restrict__ raw, uint64_t P, int scan_mode, int cos_mode, const PackConst pc,
+    const uint32_t* __restrict__ perm, PointPair* pairs, unsigned int* err,
     BlockBound* bounds, const __grid_constant__ OccSet occ) {
   static_assert(kSubPairs % 32 == 0 && kSubPairs <= 1024, "one thread per pair of a sub-block");
   __shared__ float red[kSubPairs / 32][15];
@@ -70,15 +70,15 @@ __global__ void __launch_bounds__(kSubPairs) pack_bounds_kernel(
     hi[c] = -3.0e38f;
   }
   if (k < n_pairs) {
-    const PointPair pp = pack_pair_value(raw, P, k, scan_mode, cos_mode, lx, ly, inv_cdt, err,
-                                         perm, o);
+    float rv[2][8];
+    const PointPair pp = pack_pair_value(raw, P, k, scan_mode, cos_mode, pc, err, perm, o, rv);
     pairs[k] = pp;
-    // the bounds from the packed record (no second FP64 evaluation): the
-    // laser-leg offset as packed, and "can carry weight" as a nonzero packed
-    // weight factor (zero for albedo or area 0, a point facing away from the
-    // laser, or one hidden from it)
+    // the bounds from the packed record and the raw values already loaded:
+    // the laser-leg offset as packed, and "can carry weight" as a nonzero
+    // packed weight factor (zero for albedo or area 0, a point facing away
+    // from the laser, or one hidden from it)
     for (int h = 0; h < 2 && 2 * k + h < P; ++h) {
-      const float* r = raw + 8 * (perm ? (uint64_t)perm[2 * k + h] : 2 * k + h);
+      const float* r = rv[h];
       const float kq = h ? pp.kq.y : pp.kq.x, na = h ? pp.na.y : pp.na.x;
       const float nb = h ? pp.nb.y : pp.nb.x, nc = h ? pp.nc.y : pp.nc.x;
       const float v[7] = {r[0], r[1], r[2], r[3], r[4], r[5], h ? pp.uoff.y : pp.uoff.x};
@@ -134,10 +134,10 @@ cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st) {
   scan_kernel<<<1, 1024, 0, st>>>(counts);
   scatter_kernel<<<grid_for(P, 256, s.num_sms), 256, 0, st>>>(s.cell, P, counts, s.perm);
   const uint64_t n_pairs = (P + 1) / 2;
-  const double lx = s.params.laser_x, ly = s.params.laser_y, inv_cdt = 1.0 / g.cdt;
+  const PackConst pc = pack_const(s.params.laser_x, s.params.laser_y, 1.0 / g.cdt);
   const uint64_t n_sub = (n_pairs + kSubPairs - 1) / kSubPairs;
   pack_bounds_kernel<<<(unsigned)n_sub, kSubPairs, 0, st>>>(
-      s.raw_points, P, g.scan_mode, g.cos_mode, lx, ly, inv_cdt, s.perm, s.pairs, &s.scratch->err,
+      s.raw_points, P, g.scan_mode, g.cos_mode, pc, s.perm, s.pairs, &s.scratch->err,
       s.bounds, s.occ);
   return cudaGetLastError();
 }

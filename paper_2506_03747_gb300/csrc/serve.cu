@@ -129,7 +129,7 @@ struct __align__(16) JobDesc {
   SceneScratch* scratch;     // device
   uint64_t P, S, n;          // points, scan points, bins in the cube
   int scan_mode, cos_mode, bin_mode, noise_mode;
-  double lx, ly, inv_cdt;
+  PackConst pc;
   float peak_photons, dark, nr_db, pad0;
   uint64_t seed;
   uint32_t tag, pad1, pad2, pad3;
@@ -273,22 +273,22 @@ __device__ __noinline__ void noise_item(const JobDesc& j, uint64_t b, uint64_t e
     j.scratch->scale = scale;
     j.scratch->dark = j.dark;
   }
-  for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-    const float lam = fmaf(scale, j.fwd.tau[i], j.dark);
-    j.counts[i] = poisson_sample(lam, i, j.seed, j.tag);
-  }
+  // groups of four bins (one Philox block for their first draws); a group
+  // that straddles an item edge is drawn by both items, each keeping its bins
+  noise_groups(j.fwd.tau, j.counts, b, e, 0, scale, j.dark, j.seed, j.tag, nullptr, threadIdx.x,
+               blockDim.x);
 }
 
 // PACK: pairs [b, e) of the job (each item kind runs in its own frame, so
-// the FP64 paths' registers do not weigh on the forward's)
+// the pack's registers do not weigh on the forward's)
 __device__ __noinline__ void pack_item(const JobDesc& j, uint64_t b, uint64_t e) {
   for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x)
-    pack_pair(j.raw, j.P, k, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt,
+    pack_pair(j.raw, j.P, k, j.scan_mode, j.cos_mode, j.pc,
               const_cast<PointPair*>(j.fwd.pairs), &j.scratch->err, j.perm);
   // bounds of the sub-blocks this item packs (items start on sub-block edges)
   const uint64_t sb_end = (e + kSubPairs - 1) / kSubPairs;
   for (uint64_t sb = b / kSubPairs + (threadIdx.x >> 5); sb < sb_end; sb += blockDim.x >> 5)
-    block_bound_warp(j.raw, j.P, sb, j.scan_mode, j.cos_mode, j.lx, j.ly, j.inv_cdt, j.perm,
+    block_bound_warp(j.raw, j.P, sb, j.scan_mode, j.cos_mode, j.pc, j.perm,
                      const_cast<BlockBound*>(j.fwd.bounds) + sb);
 }
 
@@ -681,9 +681,7 @@ void fill_job(Server& sv, Request* r, JobDesc& j) {
   j.cos_mode = g.cos_mode;
   j.bin_mode = g.bin_mode;
   j.noise_mode = g.noise_mode;
-  j.lx = p.laser_x;
-  j.ly = p.laser_y;
-  j.inv_cdt = 1.0 / g.cdt;
+  j.pc = pack_const(p.laser_x, p.laser_y, 1.0 / g.cdt);
   j.peak_photons = p.peak_photons;
   j.dark = p.dark_per_bin;
   j.nr_db = p.nr_db;

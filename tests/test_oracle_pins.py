@@ -398,8 +398,8 @@ def test_philox_avalanche():
 
 # ---------------------------------------------------------------------------
 # Poisson sampler (Eq. 18/19): mean, variance and the full pmf (chi-square)
-# against the Poisson distribution, for the Knuth (lambda < 30) and PTRS
-# (lambda >= 30) branches.
+# against the Poisson distribution, for the inversion (lambda < 30), split
+# (30 <= lambda < 150) and PTRS (lambda >= 150) branches.
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("lam", [1e-3, 0.5, 3.0, 9.9, 27.5, 29.9, 30.0, 100.0, 1500.0])
 def test_poisson_sampler_distribution(lam):
@@ -424,6 +424,31 @@ def test_poisson_sampler_distribution(lam):
     chi2 = ((obs[keep] - e) ** 2 / e).sum()
     dof = max(1, keep.sum() - 1)
     assert stats.chi2.sf(chi2, dof) > 1e-4
+
+
+def test_poisson_first_draw_layout():
+    """Bin i's first uniform is word (i mod 4) of the Philox block at counter
+    (i // 4, 0, tag) (words from the generator pinned above): for lambda < 30
+    the count is 0 exactly when u <= p0 = exp(-lambda) and at most 1 exactly
+    when u <= p0 (1 + lambda), bin by bin on an unaligned range (a decision
+    within 4 ulp of a threshold is skipped: expf may round either way)."""
+    n, base, seed, tag = 8192, 4 * 1000 + 2, 0x1234_5678_9ABC, 5
+    for lam in (0.05, 0.7, 3.0):
+        x = oracle.poisson(np.full(n, lam, dtype=np.float32), base, seed, tag)
+        idx = base + np.arange(n, dtype=np.uint64)
+        g = idx >> np.uint64(2)
+        ctr = np.stack([g & np.uint64(0xFFFFFFFF), g >> np.uint64(32), np.zeros(n, np.uint64),
+                        np.full(n, tag, np.uint64)], axis=1).astype(np.uint32)
+        words = oracle.philox(ctr, (seed & 0xFFFFFFFF, seed >> 32))
+        w = words[np.arange(n), (idx & np.uint64(3)).astype(np.int64)]
+        u = ((w >> 9).astype(np.float64) + 0.5) * 2.0 ** -23
+        p0 = math.exp(-float(np.float32(lam)))
+        f1 = p0 * (1.0 + float(np.float32(lam)))
+        tol = 4 * 2.0 ** -24
+        far0, far1 = np.abs(u - p0) > tol, np.abs(u - f1) > tol
+        assert far0.mean() > 0.99 and far1.mean() > 0.99
+        np.testing.assert_array_equal((x == 0)[far0], (u <= p0)[far0])
+        np.testing.assert_array_equal((x <= 1)[far1], (u <= f1)[far1])
 
 
 def test_poisson_dark_only_zero_probability_and_streams():
