@@ -60,7 +60,7 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #define NLOS_FWD_LIST_MIN 2                 // live-unit list: entries per chunk, at least
 #endif
 #ifndef NLOS_FWD_LIST_MAX
-#define NLOS_FWD_LIST_MAX 64                // ... and at most
+#define NLOS_FWD_LIST_MAX 32                // ... and at most
 #endif
 #ifndef NLOS_FWD_CONTIG
 #define NLOS_FWD_CONTIG 1                   // each warp takes a contiguous run of a block's pairs
