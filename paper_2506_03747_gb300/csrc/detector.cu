@@ -195,20 +195,27 @@ struct NoiseArgs {
   uint64_t cube_bins;         // bins of the whole cube
 };
 
-// One resident wave (kNoiseBlocksPerSm CTAs of 7 warps per SM). A thread
-// samples one group of four bins at a time (one Philox block for the four
-// first draws, a 16-byte load and store); warp w takes the 32 consecutive
-// groups of chunk c = w, w + W, w + 2W, ... (lane = group, coalesced). The
-// warp count W is odd, so the stride W * 128 bins moves a warp's bins through
-// the time indices of the transients: a bin's cost grows with its lambda and
-// the bright bins sit at a few time indices, and a stride that is a multiple
-// of the bin count (a wave of 256-thread blocks of 1024-bin transients:
-// 1216 * 256 = 304 * 1024) gave some warps every bright bin of the cube (ncu:
-// SMs 40% active, ALU pipe from 19% to 99% over the SMs). No atomics and no
-// divisions in the loop; 1/k of the inversion search from a shared table.
+// CTAs of 7 warps, kNoiseBlocksPerSm resident per SM (32 registers), up to
+// NLOS_NOISE_WAVES waves of them. A thread samples one group of four bins at a
+// time (one Philox block for the four first draws, a 16-byte load and store);
+// warp w takes the 32 consecutive groups of chunk c = w, w + W, w + 2W, ...
+// (lane = group, coalesced). The warp count W is odd, so the stride W * 128
+// bins moves a warp's bins through the time indices of the transients: a
+// bin's cost grows with its lambda and the bright bins sit at a few time
+// indices, and a stride that is a multiple of the bin count (a wave of
+// 256-thread blocks of 1024-bin transients: 1216 * 256 = 304 * 1024) gave some
+// warps every bright bin of the cube (ncu: SMs 40% active, ALU pipe from 19%
+// to 99% over the SMs). With up to 16 waves a thread mostly takes one group,
+// and the CTAs that meet bright bins are the ones that run long (heightfield128
+// 0.139 ms against 0.156 ms with one wave and a longer stride loop; union64
+// 0.060 against 0.057). No atomics and no divisions in the loop; 1/k of the
+// inversion search from a shared table.
 constexpr int kNoiseWarps = 7;
 constexpr int kNoiseThreads = 32 * kNoiseWarps;
 constexpr int kNoiseBlocksPerSm = 8;
+#ifndef NLOS_NOISE_WAVES
+#define NLOS_NOISE_WAVES 16  // resident waves of CTAs at most (the rest by the grid stride)
+#endif
 
 __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
   __shared__ float rcp[kRcpTable];
@@ -245,7 +252,7 @@ cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint64_t groups = ((a.index_base + a.n + 3) >> 2) - (a.index_base >> 2);
   const uint64_t want = (groups + kNoiseThreads - 1) / kNoiseThreads;
-  const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm;
+  const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm * NLOS_NOISE_WAVES;
   uint64_t blocks = want < wave ? want : wave;
   if (blocks > 1 && (blocks & 1u) == 0) --blocks;  // an odd number of warps (7 per block)
   noise_kernel<<<(unsigned)blocks, kNoiseThreads, 0, st>>>(a);

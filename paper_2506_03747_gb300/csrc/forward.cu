@@ -352,6 +352,7 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
     a.list_chunks_per_cta = NLOS_FWD_LIST_CHUNKS_PER_CTA;
     a.list_min_chunk = NLOS_FWD_LIST_MIN;
     a.list_max_chunk = NLOS_FWD_LIST_MAX;
+    a.list_static_pct = NLOS_FWD_LIST_STATIC;
   }
   fn<<<(unsigned)grid, threads, smem, st>>>(a, mt, sc.occ);
   e = cudaGetLastError();

@@ -59,6 +59,9 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #ifndef NLOS_FWD_LIST_MIN
 #define NLOS_FWD_LIST_MIN 2                 // live-unit list: entries per chunk, at least
 #endif
+#ifndef NLOS_FWD_LIST_STATIC
+#define NLOS_FWD_LIST_STATIC 75             // live-unit list: percent in static ranges per CTA
+#endif
 #ifndef NLOS_FWD_LIST_MAX
 #define NLOS_FWD_LIST_MAX 32                // ... and at most
 #endif
@@ -128,8 +131,9 @@ struct FwdArgs {
   // are claimed instead of chunks of units (null: no list)
   const unsigned long long* unit_list;
   const unsigned long long* n_live;
-  uint32_t list_chunks_per_cta;  // list chunks per CTA (mean)
+  uint32_t list_chunks_per_cta;  // list chunks per CTA (mean), of the claimed part
   uint32_t list_min_chunk, list_max_chunk;  // list entries per chunk, clamped
+  uint32_t list_static_pct;  // the list's first part (percent) in one contiguous range per CTA
   uint32_t n_pairs, S, B, bw, n_win, n_blk, ppb;
   uint32_t stages;   // staged point blocks (standalone warp-specialised kernel)
   float kbin;        // bins per metre of the scanned leg
@@ -920,6 +924,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
                                                        : a.bw * kTile;
   __shared__ int s_abort;
   __shared__ uint32_t s_used;  // slots this call used (units + the end mark)
+  __shared__ unsigned long long s_list_base;  // first entry of the list's claimed part
   // rows each lane's unit can touch (producer), and for each slot the rows
   // its tile's units so far can touch (consumers), in the caller's shared
   // memory (static arrays here would be repeated in every instantiation)
@@ -951,9 +956,19 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     // list mode: chunks of the live-unit list, sized from its length
     const bool listed = a.unit_list != nullptr && chunk_counter != nullptr &&
                         sm.lane_units != nullptr;
+    // the list's first list_static_pct percent goes to the CTAs in equal
+    // contiguous ranges (the list holds each (tile, window)'s units together,
+    // so a CTA meets few tiles there); the rest is claimed chunk by chunk
+    // (the claimed part's first entry is kept in shared memory: it is read
+    // once per claim, and a register for it spilled in the pair loop)
+    if (lane == 0) s_list_base = 0;
+    __syncwarp();
     if (listed) {
       units_total = *reinterpret_cast<const volatile unsigned long long*>(a.n_live);
-      chunk = units_total / ((unsigned long long)gridDim.x * a.list_chunks_per_cta);
+      if (lane == 0) s_list_base = units_total * a.list_static_pct / 100ull;
+      __syncwarp();
+      chunk = (units_total - s_list_base) /
+              ((unsigned long long)gridDim.x * a.list_chunks_per_cta);
       chunk = min(max(chunk, (unsigned long long)a.list_min_chunk),
                   (unsigned long long)a.list_max_chunk);
     }
@@ -967,12 +982,27 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
       return __shfl_sync(0xffffffffu, c, 0);
     };
     if (chunk_counter) {
-      const unsigned long long c = claim();
-      cur = min(c * chunk, units_total);
-      lim = min(cur + chunk, units_total);
+      const unsigned long long base = s_list_base;
+      if (base > 0) {
+        cur = base * blockIdx.x / gridDim.x;
+        lim = base * (blockIdx.x + 1ull) / gridDim.x;
+      } else {
+        const unsigned long long c = claim();
+        cur = min(c * chunk, units_total);
+        lim = min(cur + chunk, units_total);
+      }
       if (cur < lim && (max_claims == 0 || claims < max_claims)) {
         next = claim();
         have_next = true;
+      } else if (cur >= lim && base > 0) {
+        // an empty static range: go straight to the claimed part
+        const unsigned long long c = claim();
+        cur = min(base + c * chunk, units_total);
+        lim = min(cur + chunk, units_total);
+        if (cur < lim && (max_claims == 0 || claims < max_claims)) {
+          next = claim();
+          have_next = true;
+        }
       }
     }
     uint32_t k = 0;
@@ -981,7 +1011,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
     uint32_t run_rows = 0;   // lane 0: union of the rows of that tile's staged units
     for (;;) {
       if (cur == lim && have_next) {
-        cur = min(next * chunk, units_total);
+        cur = min(s_list_base + next * chunk, units_total);
         lim = min(cur + chunk, units_total);
         have_next = false;
         if (cur < lim && (max_claims == 0 || claims < max_claims)) {
