@@ -147,13 +147,14 @@ class ClockSampler:
 
 FORWARD_SOURCES = ("forward.cu", "forward_core.cuh", "device_util.cuh", "common.cuh")
 # FP32 issue slots per (scan point, point) pair of the moment-form adjoint
-# kernel, counted from its source: the two legs' differences, squared lengths
-# and square roots (4 + 6 + 8), the normals' dot products (6), each leg's
-# reciprocal, cosine, its derivative and the 1/r^2 factor (2 x 18), the weight
+# kernel, counted from its source: per leg the differences, squared length
+# and square root (2 + 3 + 4), the normal's dot product (3), the reciprocal,
+# cosine, its derivative and the 1/r^2 factor (18), 30 a leg; then the weight
 # and its two derivatives (8), u and du/d(delta) (4), the moment row and c (5),
-# two 6-term Horner evaluations and G1 (12), the two products (4): about 93,
-# rounded to 90 (a few of these are integer or select instructions).
-ADJ_FP32_SLOTS_PER_PAIR = 90
+# two 6-term Horner evaluations and G1 (12), the two products (4), 33 in all.
+# A confocal scan has one leg (the laser spot is the detector spot): 63; a
+# non-confocal one two: 93 (a few of these are integer or select instructions).
+ADJ_FP32_SLOTS_PER_PAIR = {"confocal": 63, "nonconfocal": 93}
 
 
 def forward_sources_sha256() -> str:
@@ -723,14 +724,15 @@ def splat_adjoint_bench(steps: int, warmup: int, peaks=None):
                           "counted on the host on 128 sampled scan points per scene"}
         # FP32 roofline of the adjoint (moment form): every (scan point, point)
         # pair is evaluated, at ADJ_FP32_SLOTS_PER_PAIR FP32 issue slots each
-        adj_peak = (props.multi_processor_count * peaks["ffma"] * f_max
-                    / ADJ_FP32_SLOTS_PER_PAIR)
+        slots = ADJ_FP32_SLOTS_PER_PAIR[params.get("scan_mode", "confocal")]
+        adj_peak = props.multi_processor_count * peaks["ffma"] * f_max / slots
         adj = steps * pairs / b
         out["adjoint_roofline"] = {
             "bound": "alu", "achieved": adj / 1e9, "peak": adj_peak / 1e9, "unit": "Gpair/s",
             "frac": adj / adj_peak,
             "peak_basis": f"{props.multi_processor_count} SMs x {peaks['ffma']:.1f} FMA lanes/clk "
-                          f"(measured) x 2070 MHz / {ADJ_FP32_SLOTS_PER_PAIR} slots per pair",
+                          f"(measured) x 2070 MHz / {slots} slots per pair "
+                          f"({params.get('scan_mode', 'confocal')} scan)",
             "work_basis": "all S x P pairs (the adjoint culls none); its time includes the "
                           "moment-table kernel; 48 B per pair gathered from the L2-resident "
                           "moment tables"}

@@ -167,12 +167,20 @@ __global__ void __launch_bounds__(256)
                 area = q[7];
     // laser leg l -> x and detector leg d -> x
     const float vlx = x - lx, vly = y - ly, vlz = z;
-    const float vdx = x - dx_s, vdy = y - dy_s, vdz = z;
     const float rl = sqrtf(vlx * vlx + vly * vly + vlz * vlz);
-    const float rd = sqrtf(vdx * vdx + vdy * vdy + vdz * vdz);
-    float Fl, dFl, cl, Fd, dFd, cd;
+    float Fl, dFl, cl, Fd, dFd, cd, rd;
     leg(a.cos_mode, nx * vlx + ny * vly + nz * vlz, vlz, nz, rl, Fl, dFl, cl);
-    leg(a.cos_mode, nx * vdx + ny * vdy + nz * vdz, vdz, nz, rd, Fd, dFd, cd);
+    if (a.scan_mode == NLOS_CONFOCAL) {
+      // the laser spot is the detector spot: the second leg is the first
+      rd = rl;
+      Fd = Fl;
+      dFd = dFl;
+      cd = cl;
+    } else {
+      const float vdx = x - dx_s, vdy = y - dy_s, vdz = z;
+      rd = sqrtf(vdx * vdx + vdy * vdy + vdz * vdz);
+      leg(a.cos_mode, nx * vdx + ny * vdy + nz * vdz, vdz, nz, rd, Fd, dFd, cd);
+    }
     const float qw = rho * area;
     const float w = qw * Fl * Fd;
     const float dw_drho = area * Fl * Fd;
