@@ -157,6 +157,15 @@ FORWARD_SOURCES = ("forward.cu", "forward_core.cuh", "device_util.cuh", "common.
 ADJ_FP32_SLOTS_PER_PAIR = {"confocal": 63, "nonconfocal": 93}
 
 
+def launches_per_step(split: bool) -> int:
+    """Kernels of this library one bench step launches: the ingest (bounding
+    box, Morton cells, the scan of the cell counts, the scatter, pack + block
+    bounds), the forward (live-unit list, pair histogram), and the detect step
+    (reduce; noise and its second pass over the deferred bright bins); a split
+    cube reduces through nlos_reduce, which adds the statistics copy kernel."""
+    return 5 + 2 + (4 if split else 3)
+
+
 def forward_sources_sha256() -> str:
     """One SHA-256 over the sources the forward kernel is compiled from."""
     h = hashlib.sha256()
@@ -477,7 +486,7 @@ def run_ours(args):
                                         f"statistics before the noise)") if split else
                            f"{ws} independent scenes, one per GPU"),
             "transients_per_s": head["transients_per_s"], "wall_s": head["wall_s"],
-            "clocks": head["clocks"], "gpu_launches": 8 * args.steps,
+            "clocks": head["clocks"], "gpu_launches": launches_per_step(split) * args.steps,
             "phase_ms": head["phase_ms"], "roofline": head["roofline"], "e2e": head["e2e"]}
     if peaks:
         line["device_peaks_per_sm_clock"] = peaks

@@ -193,6 +193,7 @@ struct NoiseArgs {
   float peak_photons, dark_cfg, nr_db;
   const double* cube_stats;   // part of a larger cube: {max, sum, sumsq} of the whole
   uint64_t cube_bins;         // bins of the whole cube
+  DeferList defer;            // deferred bright bins (defer.hdr null: one pass)
 };
 
 // CTAs of 7 warps, kNoiseBlocksPerSm resident per SM (32 registers), up to
@@ -217,32 +218,69 @@ constexpr int kNoiseBlocksPerSm = 8;
 #define NLOS_NOISE_WAVES 16  // resident waves of CTAs at most (the rest by the grid stride)
 #endif
 
-__global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
-  __shared__ float rcp[kRcpTable];
-  fill_rcp_table(rcp, threadIdx.x, blockDim.x);
-  float scale = a.scale, dark = a.dark;
+#ifndef NLOS_NOISE_DEFER
+#define NLOS_NOISE_DEFER 1  // bins with lambda >= 30 sampled by a second kernel
+#endif
+
+// The noise scale and dark level of a launch (the same in every thread and
+// in both kernels of a launch).
+__device__ __forceinline__ void launch_scale(const NoiseArgs& a, float& scale, float& dark) {
+  scale = a.scale;
+  dark = a.dark;
   if (a.cube_stats) {
     scale = noise_scale_of((float)a.cube_stats[0], a.cube_stats[1], a.cube_stats[2], a.mode,
                            a.peak_photons, a.nr_db, a.cube_bins);
     dark = a.dark_cfg;
-    if (a.scratch && blockIdx.x == 0 && threadIdx.x == 0) {
-      a.scratch->scale = scale;
-      a.scratch->dark = dark;
-    }
   } else if (a.scratch) {
     scale = noise_scale_from(a.scratch, a.mode, a.peak_photons, a.nr_db, a.n);
     dark = a.dark_cfg;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.scratch->scale = scale;
-      a.scratch->dark = dark;
-    }
+  }
+}
+
+template <bool DEFER>
+__global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
+  __shared__ float rcp[kRcpTable];
+  fill_rcp_table(rcp, threadIdx.x, blockDim.x);
+  float scale, dark;
+  launch_scale(a, scale, dark);
+  if (a.scratch && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.scratch->scale = scale;
+    a.scratch->dark = dark;
   }
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * kNoiseWarps * 32;
   const uint64_t j0 = ((uint64_t)blockIdx.x * kNoiseWarps + (threadIdx.x >> 5)) * 32 +
                       (threadIdx.x & 31);
-  noise_groups(a.tau, a.counts, 0, a.n, a.index_base, scale, dark, a.seed, a.tag, rcp, j0,
-               stride);
+  noise_groups<DEFER>(a.tau, a.counts, 0, a.n, a.index_base, scale, dark, a.seed, a.tag, rcp, j0,
+                      stride, &a.defer);
+}
+
+// Second pass (after noise_kernel, in stream order): one thread per listed
+// bin (the cube's bright bins, about 1% of them), then one warp per listed
+// region of a warp whose bins did not fit the list.
+constexpr int kDeferThreads = 256;
+
+__global__ void __launch_bounds__(kDeferThreads) noise_deferred_kernel(const NoiseArgs a) {
+  __shared__ float rcp[kRcpTable];
+  fill_rcp_table(rcp, threadIdx.x, blockDim.x);
+  float scale, dark;
+  launch_scale(a, scale, dark);
+  __syncthreads();
+  const DeferList& d = a.defer;
+  const unsigned long long claimed = *(volatile unsigned long long*)&d.hdr[0];
+  const unsigned long long nd = claimed < d.cap ? claimed : d.cap;
+  const uint64_t nt = (uint64_t)gridDim.x * kDeferThreads;
+  for (uint64_t k = (uint64_t)blockIdx.x * kDeferThreads + threadIdx.x; k < nd; k += nt) {
+    const uint32_t l = d.bins[k];
+    if (l != kDeferredCount)
+      noise_deferred_bin(a.tau, a.counts, l, a.index_base, scale, dark, a.seed, a.tag, rcp);
+  }
+  const unsigned long long nr = *(volatile unsigned long long*)&d.hdr[1];
+  const uint64_t nw = nt / 32;
+  for (uint64_t k = (uint64_t)blockIdx.x * (kDeferThreads / 32) + (threadIdx.x >> 5); k < nr;
+       k += nw)
+    noise_deferred_warp(a.tau, a.counts, a.n, d.regions[k], a.index_base, scale, dark, a.seed,
+                        a.tag, rcp);
 }
 
 cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
@@ -255,8 +293,48 @@ cudaError_t launch_noise_impl(const NoiseArgs& a, cudaStream_t st) {
   const uint64_t wave = (uint64_t)sms * kNoiseBlocksPerSm * NLOS_NOISE_WAVES;
   uint64_t blocks = want < wave ? want : wave;
   if (blocks > 1 && (blocks & 1u) == 0) --blocks;  // an odd number of warps (7 per block)
-  noise_kernel<<<(unsigned)blocks, kNoiseThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  // the deferred-bin lists: the header, a dense list of local indices for
+  // about 3% of the bins, and one entry per warp region for the warps whose
+  // bins overflow it (the regions of 32 groups cover the launch's groups, plus
+  // one for an unaligned start); one stream-ordered allocation, freed after
+  // the second pass. Without it (or for parts of 2^32 - 1 bins or more) every
+  // bin is sampled in one pass.
+  NoiseArgs b = a;
+  b.defer = DeferList{};
+  cudaError_t e = cudaSuccess;
+  if (NLOS_NOISE_DEFER && a.n < 0xFFFFFFFFull) {
+    const uint64_t cap = std::min<uint64_t>(a.n, a.n / 32 + 4096);
+    const uint64_t n_reg = groups / 32 + 2;
+    const size_t bytes = 2 * sizeof(unsigned long long) + n_reg * sizeof(unsigned long long) +
+                         ((cap * sizeof(uint32_t) + 15) & ~(size_t)15);
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess) {
+      (void)cudaGetLastError();  // no lists: one pass
+    } else if ((e = cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned long long), st)) !=
+               cudaSuccess) {
+      cudaFreeAsync(buf, st);
+      return e;
+    } else {
+      b.defer.hdr = static_cast<unsigned long long*>(buf);
+      b.defer.regions = b.defer.hdr + 2;
+      b.defer.bins = reinterpret_cast<uint32_t*>(b.defer.regions + n_reg);
+      b.defer.cap = (uint32_t)cap;
+    }
+  }
+  if (b.defer.hdr)
+    noise_kernel<true><<<(unsigned)blocks, kNoiseThreads, 0, st>>>(b);
+  else
+    noise_kernel<false><<<(unsigned)blocks, kNoiseThreads, 0, st>>>(b);
+  e = cudaGetLastError();
+  if (b.defer.hdr) {
+    if (e == cudaSuccess) {
+      noise_deferred_kernel<<<(unsigned)(sms * 4), kDeferThreads, 0, st>>>(b);
+      e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(b.defer.hdr, st);
+    if (e == cudaSuccess) e = ef;
+  }
+  return e;
 }
 
 cudaError_t launch_noise(const float* tau, uint64_t n, float scale, float dark, uint64_t seed,

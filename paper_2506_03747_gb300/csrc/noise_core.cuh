@@ -164,11 +164,30 @@ __device__ __forceinline__ void fill_rcp_table(float* rcp, int t, int nthreads) 
 // groups of four global indices that meet [b, e), computes each group's
 // Philox block once, and samples its (up to four) bins of the range. Interior
 // groups of an aligned part load and store four bins at a time.
+// DEFER: bins with lambda >= 30 get kDeferredCount instead of their count (a
+// second pass, noise_deferred_warp, samples them), so the first pass holds no
+// out-of-line call and keeps its registers for the common bins.
+constexpr uint32_t kDeferredCount = 0xFFFFFFFFu;
+
+// Where DEFER puts the deferred bins: a dense list of their local indices
+// (count in hdr[0], at most cap entries) and, for a warp whose bins no longer
+// fit, the first group of its 32-group region (count in hdr[1]); the lanes of
+// a warp take consecutive groups (j0 = 32 * warp + lane, stride a multiple of
+// 32), so the lanes still in the loop are always a prefix of the warp.
+struct DeferList {
+  unsigned long long* hdr;       // [2]: dense entries claimed, regions listed
+  uint32_t* bins;                // [cap] local bin indices (kDeferredCount: skip)
+  unsigned long long* regions;   // first groups of overflowed warp regions
+  uint32_t cap;
+};
+
+template <bool DEFER = false>
 __device__ __forceinline__ void noise_groups(const float* __restrict__ tau,
                                              uint32_t* __restrict__ counts, uint64_t b, uint64_t e,
                                              uint64_t index_base, float scale, float dark,
                                              uint64_t seed, uint32_t tag, const float* rcp,
-                                             uint64_t j0, uint64_t stride) {
+                                             uint64_t j0, uint64_t stride,
+                                             const DeferList* dl = nullptr) {
   if (b >= e) return;
   const uint64_t gb = (index_base + b) >> 2, ge = (index_base + e + 3) >> 2;
   const bool vec_ok = ((((uintptr_t)tau) | ((uintptr_t)counts)) & 15u) == 0;
@@ -195,8 +214,46 @@ __device__ __forceinline__ void noise_groups(const float* __restrict__ tau,
     for (int r = 0; r < 4; ++r) {
       // bins outside the range are not sampled
       const float lam = ((in >> r) & 1u) ? fmaf(scale, t[r], dark) : 0.0f;
-      c[r] = poisson_from(lam, word_uniform(group_word(blk, (uint32_t)r)), 4 * g + r, seed, tag,
-                          rcp);
+      const float u0 = word_uniform(group_word(blk, (uint32_t)r));
+      if (DEFER)
+        c[r] = !(lam > 0.0f) ? 0u
+               : lam < kInvMax ? poisson_inversion(lam, u0, rcp)
+                               : kDeferredCount;
+      else
+        c[r] = poisson_from(lam, u0, 4 * g + r, seed, tag, rcp);
+    }
+    if (DEFER) {
+      uint32_t dm = 0;  // bit r: bin 4g + r was deferred
+#pragma unroll
+      for (int r = 0; r < 4; ++r) dm |= (uint32_t)(c[r] == kDeferredCount) << r;
+      const uint32_t act = __activemask();
+      if (__any_sync(act, dm != 0u)) {
+        const uint32_t lane = threadIdx.x & 31u;
+        const uint32_t cnt = (uint32_t)__popc(dm);
+        uint32_t incl = cnt;  // inclusive prefix sum over the lanes (a prefix of the warp)
+#pragma unroll
+        for (uint32_t o = 1; o < 32u; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(act, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(act, incl, 31 - __clz((int)act));
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&dl->hdr[0], (unsigned long long)total);
+        base = __shfl_sync(act, base, 0);
+        const unsigned long long o0 = base + incl - cnt;
+        const bool fits = base + total <= dl->cap;  // the same in every lane
+        uint32_t o = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if ((dm >> r) & 1u) {
+            const unsigned long long slot = o0 + o++;
+            if (slot < dl->cap) dl->bins[slot] = fits ? (uint32_t)(l0 + r) : kDeferredCount;
+          }
+        if (!fits && lane == 0) {
+          const unsigned long long k = atomicAdd(&dl->hdr[1], 1ull);
+          dl->regions[k] = g - lane;  // the warp region's first group
+        }
+      }
     }
     if (vec) {
       *reinterpret_cast<uint4*>(counts + l0) = make_uint4(c[0], c[1], c[2], c[3]);
@@ -206,6 +263,57 @@ __device__ __forceinline__ void noise_groups(const float* __restrict__ tau,
         const int64_t l = l0 + r;
         if (l >= (int64_t)b && l < (int64_t)e) counts[l] = c[r];
       }
+    }
+  }
+}
+
+// Second pass, one deferred bin (local index l): the count with the bin's
+// first-pass draws (its group word and its own stream).
+__device__ __forceinline__ void noise_deferred_bin(const float* __restrict__ tau,
+                                                   uint32_t* __restrict__ counts, uint64_t l,
+                                                   uint64_t index_base, float scale, float dark,
+                                                   uint64_t seed, uint32_t tag, const float* rcp) {
+  const uint64_t i = index_base + l;
+  const float lam = fmaf(scale, __ldg(tau + l), dark);
+  const uint4 blk = group_block(i >> 2, seed, tag);
+  counts[l] = poisson_large(lam, word_uniform(group_word(blk, (uint32_t)(i & 3u))), i, seed, tag,
+                            rcp);
+}
+
+// Second pass over one 32-group region (global bins 4 G0 .. 4 G0 + 127; local
+// index l = global - index_base, inside [0, n)) by one warp: the bins the first
+// pass marked kDeferredCount (lambda >= 30) are dealt out to the lanes, one bin
+// a lane at a time, and sampled with the same draws (the bin's group word and
+// its own stream), so bright runs of bins are searched side by side.
+__device__ __forceinline__ void noise_deferred_warp(const float* __restrict__ tau,
+                                                    uint32_t* __restrict__ counts, uint64_t n,
+                                                    uint64_t G0, uint64_t index_base,
+                                                    float scale, float dark, uint64_t seed,
+                                                    uint32_t tag, const float* rcp) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t w0 = (int64_t)(4 * G0) - (int64_t)index_base;
+  uint32_t m[4];
+  uint32_t total = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t l = w0 + 32 * r + (int64_t)lane;
+    const bool d = l >= 0 && l < (int64_t)n && counts[l] == kDeferredCount;
+    m[r] = __ballot_sync(0xffffffffu, d);
+    total += (uint32_t)__popc(m[r]);
+  }
+  for (uint32_t base = 0; base < total; base += 32u) {
+    uint32_t k = base + lane;  // this lane's deferred bin, in order
+    if (k < total) {
+      int r = 0;
+      while (k >= (uint32_t)__popc(m[r])) {
+        k -= (uint32_t)__popc(m[r]);
+        ++r;
+      }
+      uint32_t mm = m[r];
+      for (uint32_t j = 0; j < k; ++j) mm &= mm - 1u;  // drop the k lowest set bits
+      const uint32_t src = (uint32_t)__ffs((int)mm) - 1u;
+      const int64_t l = w0 + 32 * r + (int64_t)src;
+      noise_deferred_bin(tau, counts, (uint64_t)l, index_base, scale, dark, seed, tag, rcp);
     }
   }
 }
