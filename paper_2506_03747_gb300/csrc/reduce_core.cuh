@@ -33,9 +33,21 @@ __device__ __forceinline__ void df_add(float x, float& sh, float& sl, float& qh,
   ql = __fadd_rn(ql, __fadd_rn(e, pe));
 }
 
+// (ah, al) += (bh, bl) for unevaluated FP32 pairs: the error-free sum of the
+// high parts, the low parts and that sum's error added, then renormalised
+// (|lo| <= half an ulp of hi), so a pair keeps about 48 bits.
+__device__ __forceinline__ void df_add_pair(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  ah = __fadd_rn(s, e);
+  al = __fsub_rn(e, __fsub_rn(ah, s));
+}
+
 // One warp's sums over a transient row of B bins (every lane returns the
 // warp's values): the FP64 sum and sum of squares of the FP32 bins (lane
-// sums as above, then a fixed FP64 shuffle tree) and the maximum.
+// sums as above, combined over the lanes by a fixed shuffle tree of pair
+// additions, and converted to FP64 once) and the maximum.
 __device__ __forceinline__ void trace_sums(const float* __restrict__ row, uint32_t B, int lane,
                                            double& s_out, double& q_out, float& m_out) {
   float sh = 0.f, sl = 0.f, qh = 0.f, ql = 0.f;
@@ -57,15 +69,27 @@ __device__ __forceinline__ void trace_sums(const float* __restrict__ row, uint32
       m = fmaxf(m, v);
     }
   }
-  double s = (double)sh + (double)sl, q = (double)qh + (double)ql;
+  // renormalise the lane pairs (lo accumulated plain roundings)
+  {
+    float t = __fadd_rn(sh, sl);
+    sl = __fsub_rn(sl, __fsub_rn(t, sh));
+    sh = t;
+    t = __fadd_rn(qh, ql);
+    ql = __fsub_rn(ql, __fsub_rn(t, qh));
+    qh = t;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float bsh = __shfl_xor_sync(0xffffffffu, sh, o);
+    const float bsl = __shfl_xor_sync(0xffffffffu, sl, o);
+    const float bqh = __shfl_xor_sync(0xffffffffu, qh, o);
+    const float bql = __shfl_xor_sync(0xffffffffu, ql, o);
+    df_add_pair(sh, sl, bsh, bsl);
+    df_add_pair(qh, ql, bqh, bql);
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   }
-  s_out = s;
-  q_out = q;
+  s_out = (double)sh + (double)sl;
+  q_out = (double)qh + (double)ql;
   m_out = m;
 }
 
