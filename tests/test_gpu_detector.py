@@ -153,6 +153,38 @@ def test_noise_statistics_full_pipeline():
         assert abs(tot - expect) < 5 * np.sqrt(expect) + 1
 
 
+def test_poisson_unaligned_ranges_and_deferred_bins():
+    """Unaligned parts (index_base not a multiple of 4, a ragged length, a
+    misaligned tau/counts view) and cubes whose bright bins (lambda >= 30,
+    sampled by the second pass) are few, many (past the dense list, so whole
+    warp regions go to the second pass) or all: counts equal the oracle's bin
+    for bin, and no deferral marker is left."""
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    rng = np.random.default_rng(11)
+    n = 100_003
+    base = rng.random(n + 1).astype(np.float32)
+    for frac_bright, lam_hi in [(0.005, 120.0), (0.2, 90.0), (1.0, 45.0), (0.01, 400.0)]:
+        tau = (base * 20.0).astype(np.float32)
+        bright = rng.random(n + 1) < frac_bright
+        tau[bright] = (30.0 + (lam_hi - 30.0) * rng.random(bright.sum())).astype(np.float32)
+        for index_base, off in [(1003, 1), (4 * 7 + 2, 0)]:
+            t_full = torch.from_numpy(tau).cuda()
+            t = t_full[off:off + n]
+            c_full = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+            c = c_full[off:off + n]
+            nlos.noise(t, n, 1.0, 0.0, seed=77, stream_tag=3, index_base=index_base, counts=c)
+            torch.cuda.synchronize()
+            got = c.cpu().numpy().view(np.uint32)
+            lam = oracle.lam_from(tau[off:off + n].astype(np.float64), np.float32(1.0),
+                                  np.float32(0.0))
+            ref = oracle.poisson(lam, index_base, 77, 3)
+            diff = int((got != ref).sum())
+            print("bright", frac_bright, "base", index_base, "differing", diff)
+            assert not (got == 0xFFFFFFFF).any()
+            assert diff <= 3
+
+
 def test_pipeline_counts_match_oracle_bins():
     """Counts of the whole pipeline against the oracle's sampler fed the GPU's
     own expected counts (lambda = scale * tau_G + dark, rounded to float): the
