@@ -239,15 +239,17 @@ __device__ __forceinline__ void launch_scale(const NoiseArgs& a, float& scale, f
 
 template <bool DEFER>
 __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel(const NoiseArgs a) {
-  __shared__ float rcp[kRcpTable];
-  fill_rcp_table(rcp, threadIdx.x, blockDim.x);
+  // one table per warp, so that no CTA barrier is needed (CTAs are short)
+  __shared__ float rcp_tab[kNoiseWarps][kRcpTable];
+  float* rcp = rcp_tab[threadIdx.x >> 5];
+  fill_rcp_table(rcp, threadIdx.x & 31, 32);
+  __syncwarp();
   float scale, dark;
   launch_scale(a, scale, dark);
   if (a.scratch && blockIdx.x == 0 && threadIdx.x == 0) {
     a.scratch->scale = scale;
     a.scratch->dark = dark;
   }
-  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * kNoiseWarps * 32;
   const uint64_t j0 = ((uint64_t)blockIdx.x * kNoiseWarps + (threadIdx.x >> 5)) * 32 +
                       (threadIdx.x & 31);
@@ -261,11 +263,12 @@ __global__ void __launch_bounds__(kNoiseThreads, kNoiseBlocksPerSm) noise_kernel
 constexpr int kDeferThreads = 256;
 
 __global__ void __launch_bounds__(kDeferThreads) noise_deferred_kernel(const NoiseArgs a) {
-  __shared__ float rcp[kRcpTable];
-  fill_rcp_table(rcp, threadIdx.x, blockDim.x);
+  __shared__ float rcp_tab[kDeferThreads / 32][kRcpTable];  // one table per warp
+  float* rcp = rcp_tab[threadIdx.x >> 5];
+  fill_rcp_table(rcp, threadIdx.x & 31, 32);
+  __syncwarp();
   float scale, dark;
   launch_scale(a, scale, dark);
-  __syncthreads();
   const DeferList& d = a.defer;
   const unsigned long long claimed = *(volatile unsigned long long*)&d.hdr[0];
   const unsigned long long nd = claimed < d.cap ? claimed : d.cap;

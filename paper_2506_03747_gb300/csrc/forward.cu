@@ -78,7 +78,11 @@ __global__ void __launch_bounds__(256) unit_list_kernel(const __grid_constant__ 
     const uint32_t blk = b0 + threadIdx.x;
     const unsigned long long unit = tw * a.n_blk + blk;
     float ulo = 0.f, uhi = 0.f;
-    const bool live = blk < a.n_blk && unit_live<SCAN, COS>(a, unit, margin, ulo, uhi);
+    uint32_t dead = 0;
+    const bool live =
+        blk < a.n_blk && (a.list_halves
+                              ? unit_live_halves<SCAN, COS>(a, unit, margin, ulo, uhi, dead)
+                              : unit_live<SCAN, COS>(a, unit, margin, ulo, uhi));
     const uint32_t rows = live ? unit_rows(ulo, uhi, margin, a.bw) : 0u;
     const uint32_t m = __ballot_sync(0xffffffffu, live);
     if (lane == 0) s_warp[warp] = __popc(m);
@@ -95,7 +99,8 @@ __global__ void __launch_bounds__(256) unit_list_kernel(const __grid_constant__ 
     __syncthreads();
     if (live) {
       const uint32_t pos = s_warp[warp] + __popc(m & ((1u << lane) - 1u));
-      list[s_base + pos] = unit | ((unsigned long long)rows << 32);
+      list[s_base + pos] =
+          unit | ((unsigned long long)dead << kListHalfShift) | ((unsigned long long)rows << 32);
     }
     __syncthreads();
   }
@@ -335,6 +340,11 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   ListFn lf = (NLOS_FWD_CULL && a.bounds) ? pick_list(g.scan_mode, g.cos_mode, mode) : nullptr;
   unsigned long long* list = nullptr;
   if (lf) {
+    // halves (for the list kernel and the forward): two sub-blocks a unit,
+    // and unit numbers that leave bits 30-31 of a list entry free
+    a.list_halves = (NLOS_FWD_LIST_HALVES && a.ppb == 2 * kSubPairs &&
+                     a.units < (1ull << kListHalfShift))
+                        ? 1u : 0u;
     e = cudaMallocAsync(reinterpret_cast<void**>(&list), sizeof(unsigned long long) * a.units, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&sc.scratch->n_live, 0, sizeof(unsigned long long), st);

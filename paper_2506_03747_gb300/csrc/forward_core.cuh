@@ -62,6 +62,9 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #ifndef NLOS_FWD_LIST_STATIC
 #define NLOS_FWD_LIST_STATIC 75             // live-unit list: percent in static ranges per CTA
 #endif
+#ifndef NLOS_FWD_LIST_HALVES
+#define NLOS_FWD_LIST_HALVES 1              // live-unit list: halves of a unit culled apart
+#endif
 #ifndef NLOS_FWD_LIST_MAX
 #define NLOS_FWD_LIST_MAX 32                // ... and at most
 #endif
@@ -134,6 +137,7 @@ struct FwdArgs {
   uint32_t list_chunks_per_cta;  // list chunks per CTA (mean), of the claimed part
   uint32_t list_min_chunk, list_max_chunk;  // list entries per chunk, clamped
   uint32_t list_static_pct;  // the list's first part (percent) in one contiguous range per CTA
+  uint32_t list_halves;      // list entries carry the units' dead halves (ppb = 2 kSubPairs)
   uint32_t n_pairs, S, B, bw, n_win, n_blk, ppb;
   uint32_t stages;   // staged point blocks (standalone warp-specialised kernel)
   float kbin;        // bins per metre of the scanned leg
@@ -804,16 +808,13 @@ __device__ __forceinline__ BlockBound block_bound(const FwdArgs& a, uint32_t blk
   return b;
 }
 
+// Can a point inside the bounds b reach the window starting at bin w0 (lim
+// bins) of a tile with spot bounds t (and face one of its spots)? ulo, uhi:
+// the range of u over the two boxes, window-relative.
 template <int SCAN, int COS>
-__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin,
-                                          float& ulo_out, float& uhi_out) {
-  const unsigned long long tw = unit / a.n_blk;
-  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
-  const uint32_t tile = (uint32_t)(tw / a.n_win);
-  const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
-  const float lim = (float)min(a.bw, a.B - w0);
-  const TileBound t = a.tiles[tile];
-  const BlockBound b = block_bound(a, blk);
+__device__ __forceinline__ bool bounds_live(const FwdArgs& a, const TileBound& t,
+                                            const BlockBound& b, uint32_t w0, float lim,
+                                            float margin, float& ulo_out, float& uhi_out) {
   if (b.live == 0.f) return false;
   const float dx = fmaxf(0.f, fmaxf(b.x0 - t.sx1, t.sx0 - b.x1));
   const float dy = fmaxf(0.f, fmaxf(b.y0 - t.sy1, t.sy0 - b.y1));
@@ -837,6 +838,44 @@ __device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long u
     if (f <= 0.f) return false;
   }
   return true;
+}
+
+template <int SCAN, int COS>
+__device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long unit, float margin,
+                                          float& ulo_out, float& uhi_out) {
+  const unsigned long long tw = unit / a.n_blk;
+  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
+  const uint32_t tile = (uint32_t)(tw / a.n_win);
+  const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
+  const float lim = (float)min(a.bw, a.B - w0);
+  const TileBound t = a.tiles[tile];
+  const BlockBound b = block_bound(a, blk);
+  return bounds_live<SCAN, COS>(a, t, b, w0, lim, margin, ulo_out, uhi_out);
+}
+
+// The same test on each half of a two-sub-block unit: whether the unit is
+// live, its u range over its live halves, and the halves that are not
+// (dead bit h: no pair of half h can reach the window or face a spot).
+template <int SCAN, int COS>
+__device__ __forceinline__ bool unit_live_halves(const FwdArgs& a, unsigned long long unit,
+                                                 float margin, float& ulo_out, float& uhi_out,
+                                                 uint32_t& dead) {
+  const unsigned long long tw = unit / a.n_blk;
+  const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
+  const uint32_t tile = (uint32_t)(tw / a.n_win);
+  const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
+  const float lim = (float)min(a.bw, a.B - w0);
+  const TileBound t = a.tiles[tile];
+  const uint32_t sb0 = blk * 2u;
+  const uint32_t n_sub = (a.n_pairs + kSubPairs - 1) / kSubPairs;
+  float l0 = 0.f, h0 = 0.f, l1 = 0.f, h1 = 0.f;
+  const bool live0 = bounds_live<SCAN, COS>(a, t, a.bounds[sb0], w0, lim, margin, l0, h0);
+  const bool live1 = sb0 + 1 < n_sub &&
+                     bounds_live<SCAN, COS>(a, t, a.bounds[sb0 + 1], w0, lim, margin, l1, h1);
+  dead = (live0 ? 0u : 1u) | (live1 ? 0u : 2u);
+  ulo_out = live0 ? (live1 ? fminf(l0, l1) : l0) : l1;
+  uhi_out = live0 ? (live1 ? fmaxf(h0, h1) : h0) : h1;
+  return live0 || live1;
 }
 
 // Occluders that can meet a segment from a spot of the unit's tile (z = 0)
@@ -889,6 +928,12 @@ __device__ __forceinline__ uint32_t unit_rows(float ulo, float uhi, float margin
 // Units carry the occluder mask of MODE_NEAREST_OCC in their top bits.
 constexpr int kUnitBits = 48;
 constexpr unsigned long long kUnitMask = (1ull << kUnitBits) - 1ull;
+// A staged unit's dead halves (unit_live_halves) in tag bits 46-47, and in
+// bits 30-31 of a live-unit list entry (whose units are then below 2^30).
+constexpr int kHalfShift = 46;
+constexpr unsigned long long kUnitIdMask = (1ull << kHalfShift) - 1ull;
+constexpr int kListHalfShift = 30;
+constexpr uint32_t kListUnitMask = (1u << kListHalfShift) - 1u;
 
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -1051,8 +1096,12 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
             failed = true;
             break;
           }
-          const unsigned long long unit = listed ? sm.lane_units[j] : cur + j;
+          const unsigned long long raw_unit = listed ? sm.lane_units[j] : cur + j;
+          const unsigned long long unit =
+              (listed && a.list_halves) ? (raw_unit & kListUnitMask) : raw_unit;
           unsigned long long tag = unit;
+          if (listed && a.list_halves)
+            tag |= (unsigned long long)(raw_unit >> kListHalfShift) << kHalfShift;
           if (MODE == MODE_NEAREST_OCC)
             tag |= (unsigned long long)occ_unit_mask(a, unit, *occ) << kUnitBits;
           if (ranged) {
@@ -1117,7 +1166,7 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         break;
       }
       const unsigned long long tag = *(volatile unsigned long long*)&unit_of[slot];
-      const unsigned long long unit = tag == kNoUnit ? kNoUnit : (tag & kUnitMask);
+      const unsigned long long unit = tag == kNoUnit ? kNoUnit : (tag & kUnitIdMask);
       if (unit != kNoUnit) {
         const long long tw = (long long)(unit / a.n_blk);
         const uint32_t blk = (uint32_t)(unit - (unsigned long long)tw * a.n_blk);
@@ -1140,9 +1189,14 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         // the producer's running union for this tile, up to this unit
         if (ranged) tile_rows = s_slot_rows[slot];
         const uint32_t first = blk * a.ppb;
-        compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb,
-                                       min(a.ppb, a.n_pairs - first), cw, ncw, ts, col_addr,
-                                       cnt, mom_J, occ, (uint32_t)(tag >> kUnitBits), g);
+        const uint32_t nb = min(a.ppb, a.n_pairs - first);
+        // halves of the block the list ruled out are not evaluated
+        const uint32_t dead = (uint32_t)(tag >> kHalfShift) & 3u;
+        const uint32_t lo = (dead & 1u) ? min(nb, (uint32_t)kSubPairs) : 0u;
+        const uint32_t hi = (dead & 2u) ? min(nb, (uint32_t)kSubPairs) : nb;
+        compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb + lo,
+                                       hi > lo ? hi - lo : 0u, cw, ncw, ts, col_addr, cnt,
+                                       mom_J, occ, (uint32_t)(tag >> kUnitBits), g);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
