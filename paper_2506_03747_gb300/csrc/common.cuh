@@ -72,7 +72,7 @@ void compact_tile_order(const std::vector<ScanPoint>& plain, uint32_t nx, uint32
 //          non-confocal scan, in bins; 0 for confocal),
 //   live   1 if some point can carry weight (albedo * area > 0 and, for a
 //          non-confocal scan with object cosines, facing the laser), else 0.
-constexpr uint32_t kSubPairs = 128;
+constexpr uint32_t kSubPairs = 256;
 struct __align__(16) BlockBound {
   float x0, x1, y0, y1, z0, z1;
   float nx0, nx1, ny0, ny1, nz0, nz1;

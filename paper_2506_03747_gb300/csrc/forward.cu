@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) unit_list_kernel(const __grid_constant__ 
     uint32_t dead = 0;
     const bool live =
         blk < a.n_blk && (a.list_halves
-                              ? unit_live_subs<SCAN, COS>(a, unit, margin, ulo, uhi, dead)
+                              ? unit_live_halves<SCAN, COS>(a, unit, margin, ulo, uhi, dead)
                               : unit_live<SCAN, COS>(a, unit, margin, ulo, uhi));
     const uint32_t rows = live ? unit_rows(ulo, uhi, margin, a.bw) : 0u;
     const uint32_t m = __ballot_sync(0xffffffffu, live);
@@ -340,10 +340,9 @@ cudaError_t launch_forward(const SceneImpl& sc, float* tau, cudaStream_t st) {
   ListFn lf = (NLOS_FWD_CULL && a.bounds) ? pick_list(g.scan_mode, g.cos_mode, mode) : nullptr;
   unsigned long long* list = nullptr;
   if (lf) {
-    // sub-blocks culled apart (for the list kernel and the forward): kMaxSubs
-    // sub-blocks a unit, and unit numbers that leave bits 28-31 of a list
-    // entry free
-    a.list_halves = (NLOS_FWD_LIST_HALVES && a.ppb == kMaxSubs * kSubPairs &&
+    // halves (for the list kernel and the forward): two sub-blocks a unit,
+    // and unit numbers that leave bits 30-31 of a list entry free
+    a.list_halves = (NLOS_FWD_LIST_HALVES && a.ppb == 2 * kSubPairs &&
                      a.units < (1ull << kListHalfShift))
                         ? 1u : 0u;
     e = cudaMallocAsync(reinterpret_cast<void**>(&list), sizeof(unsigned long long) * a.units, st);

@@ -63,7 +63,7 @@ constexpr int kPairsPerBlock = 256;         // serving kernel: 16 KB per staged 
 #define NLOS_FWD_LIST_STATIC 75             // live-unit list: percent in static ranges per CTA
 #endif
 #ifndef NLOS_FWD_LIST_HALVES
-#define NLOS_FWD_LIST_HALVES 1              // live-unit list: sub-blocks of a unit culled apart
+#define NLOS_FWD_LIST_HALVES 1              // live-unit list: halves of a unit culled apart
 #endif
 #ifndef NLOS_FWD_LIST_MAX
 #define NLOS_FWD_LIST_MAX 32                // ... and at most
@@ -137,7 +137,7 @@ struct FwdArgs {
   uint32_t list_chunks_per_cta;  // list chunks per CTA (mean), of the claimed part
   uint32_t list_min_chunk, list_max_chunk;  // list entries per chunk, clamped
   uint32_t list_static_pct;  // the list's first part (percent) in one contiguous range per CTA
-  uint32_t list_halves;      // list entries carry the units' dead sub-blocks (ppb = kMaxSubs kSubPairs)
+  uint32_t list_halves;      // list entries carry the units' dead halves (ppb = 2 kSubPairs)
   uint32_t n_pairs, S, B, bw, n_win, n_blk, ppb;
   uint32_t stages;   // staged point blocks (standalone warp-specialised kernel)
   float kbin;        // bins per metre of the scanned leg
@@ -853,41 +853,29 @@ __device__ __forceinline__ bool unit_live(const FwdArgs& a, unsigned long long u
   return bounds_live<SCAN, COS>(a, t, b, w0, lim, margin, ulo_out, uhi_out);
 }
 
-// The same test on each sub-block of a unit of up to kMaxSubs sub-blocks:
-// whether the unit is live, its u range over its live sub-blocks, and the
-// sub-blocks that are not (dead bit j: no pair of sub-block j can reach the
-// window or face a spot).
-constexpr uint32_t kMaxSubs = 4;
-
+// The same test on each half of a two-sub-block unit: whether the unit is
+// live, its u range over its live halves, and the halves that are not
+// (dead bit h: no pair of half h can reach the window or face a spot).
 template <int SCAN, int COS>
-__device__ __forceinline__ bool unit_live_subs(const FwdArgs& a, unsigned long long unit,
-                                               float margin, float& ulo_out, float& uhi_out,
-                                               uint32_t& dead) {
+__device__ __forceinline__ bool unit_live_halves(const FwdArgs& a, unsigned long long unit,
+                                                 float margin, float& ulo_out, float& uhi_out,
+                                                 uint32_t& dead) {
   const unsigned long long tw = unit / a.n_blk;
   const uint32_t blk = (uint32_t)(unit - tw * a.n_blk);
   const uint32_t tile = (uint32_t)(tw / a.n_win);
   const uint32_t w0 = (uint32_t)(tw % a.n_win) * a.bw;
   const float lim = (float)min(a.bw, a.B - w0);
   const TileBound t = a.tiles[tile];
-  const uint32_t sub_per = a.ppb / kSubPairs;
-  const uint32_t sb0 = blk * sub_per;
+  const uint32_t sb0 = blk * 2u;
   const uint32_t n_sub = (a.n_pairs + kSubPairs - 1) / kSubPairs;
-  float lo = 3.0e38f, hi = -3.0e38f;
-  dead = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < kMaxSubs; ++j) {
-    if (j >= sub_per) break;
-    float l = 0.f, h = 0.f;
-    if (sb0 + j < n_sub && bounds_live<SCAN, COS>(a, t, a.bounds[sb0 + j], w0, lim, margin, l, h)) {
-      lo = fminf(lo, l);
-      hi = fmaxf(hi, h);
-    } else {
-      dead |= 1u << j;
-    }
-  }
-  ulo_out = lo;
-  uhi_out = hi;
-  return dead != (1u << sub_per) - 1u;
+  float l0 = 0.f, h0 = 0.f, l1 = 0.f, h1 = 0.f;
+  const bool live0 = bounds_live<SCAN, COS>(a, t, a.bounds[sb0], w0, lim, margin, l0, h0);
+  const bool live1 = sb0 + 1 < n_sub &&
+                     bounds_live<SCAN, COS>(a, t, a.bounds[sb0 + 1], w0, lim, margin, l1, h1);
+  dead = (live0 ? 0u : 1u) | (live1 ? 0u : 2u);
+  ulo_out = live0 ? (live1 ? fminf(l0, l1) : l0) : l1;
+  uhi_out = live0 ? (live1 ? fmaxf(h0, h1) : h0) : h1;
+  return live0 || live1;
 }
 
 // Occluders that can meet a segment from a spot of the unit's tile (z = 0)
@@ -940,11 +928,11 @@ __device__ __forceinline__ uint32_t unit_rows(float ulo, float uhi, float margin
 // Units carry the occluder mask of MODE_NEAREST_OCC in their top bits.
 constexpr int kUnitBits = 48;
 constexpr unsigned long long kUnitMask = (1ull << kUnitBits) - 1ull;
-// A staged unit's dead sub-blocks (unit_live_subs) in tag bits 44-47, and in
-// bits 28-31 of a live-unit list entry (whose units are then below 2^28).
-constexpr int kHalfShift = 44;
+// A staged unit's dead halves (unit_live_halves) in tag bits 46-47, and in
+// bits 30-31 of a live-unit list entry (whose units are then below 2^30).
+constexpr int kHalfShift = 46;
 constexpr unsigned long long kUnitIdMask = (1ull << kHalfShift) - 1ull;
-constexpr int kListHalfShift = 28;
+constexpr int kListHalfShift = 30;
 constexpr uint32_t kListUnitMask = (1u << kListHalfShift) - 1u;
 
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
@@ -1202,21 +1190,13 @@ __device__ bool fwd_run_ws(const FwdArgs& a, unsigned long long u0, unsigned lon
         if (ranged) tile_rows = s_slot_rows[slot];
         const uint32_t first = blk * a.ppb;
         const uint32_t nb = min(a.ppb, a.n_pairs - first);
-        // the runs of sub-blocks the list did not rule out (the whole block
-        // when it is not made of kMaxSubs of them), each shared out over the warps
-        const bool subs = a.ppb == kMaxSubs * kSubPairs;
-        const uint32_t sub = subs ? kSubPairs : a.ppb;
-        uint32_t live = subs ? (~(uint32_t)(tag >> kHalfShift) & 15u) : 1u;
-        while (live) {
-          const uint32_t j0 = (uint32_t)__ffs((int)live) - 1u;
-          const uint32_t run = (uint32_t)__ffs((int)~(live >> j0)) - 1u;
-          live &= ~(((1u << run) - 1u) << j0);
-          const uint32_t lo = min(nb, j0 * sub), hi = min(nb, (j0 + run) * sub);
-          if (hi > lo)
-            compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb + lo,
-                                                   hi - lo, cw, ncw, ts, col_addr, cnt, mom_J,
-                                                   occ, (uint32_t)(tag >> kUnitBits), g);
-        }
+        // halves of the block the list ruled out are not evaluated
+        const uint32_t dead = (uint32_t)(tag >> kHalfShift) & 3u;
+        const uint32_t lo = (dead & 1u) ? min(nb, (uint32_t)kSubPairs) : 0u;
+        const uint32_t hi = (dead & 2u) ? min(nb, (uint32_t)kSubPairs) : nb;
+        compute_block<SCAN, COS, MODE, UNROLL>(a, sm.stage + (size_t)slot * a.ppb + lo,
+                                       hi > lo ? hi - lo : 0u, cw, ncw, ts, col_addr, cnt,
+                                       mom_J, occ, (uint32_t)(tag >> kUnitBits), g);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
