@@ -158,12 +158,13 @@ ADJ_FP32_SLOTS_PER_PAIR = {"confocal": 63, "nonconfocal": 93}
 
 
 def launches_per_step(split: bool) -> int:
-    """Kernels of this library one bench step launches: the ingest (bounding
-    box, Morton cells, the scan of the cell counts, the scatter, pack + block
-    bounds), the forward (live-unit list, pair histogram), and the detect step
-    (reduce; noise and its second pass over the deferred bright bins); a split
-    cube reduces through nlos_reduce, which adds the statistics copy kernel."""
-    return 5 + 2 + (4 if split else 3)
+    """Kernels of this library one bench step launches: the ingest (counts and
+    box initialised, bounding box, Morton cells, the scan of the cell counts,
+    the scatter, pack + block bounds), the forward (live-unit list, pair
+    histogram), and the detect step (reduce; noise and its second pass over the
+    deferred bright bins); a split cube reduces through nlos_reduce, which adds
+    the statistics copy kernel."""
+    return 6 + 2 + (4 if split else 3)
 
 
 def forward_sources_sha256() -> str:

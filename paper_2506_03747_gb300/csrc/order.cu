@@ -10,6 +10,7 @@
 //
 // Device steps (one stream, no host synchronisation; the step routines are
 // in order_core.cuh, shared with the serving kernel):
+//   0. init: the cell counts zeroed, the box words set (one small kernel),
 //   1. box: the points' bounding box (order-preserving integer atomics),
 //   2. cell: each point's cell and the cell counts,
 //   3. scan: exclusive prefix sum of the counts (one CTA),
@@ -38,6 +39,14 @@ __global__ void cell_kernel(const float* __restrict__ raw, uint64_t P, const uin
                             uint16_t* cell, uint32_t* counts) {
   cell_range(raw, 0, P, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
              (uint64_t)gridDim.x * blockDim.x, box, cell, counts);
+}
+
+// The cell counts zeroed and the box words set to their identities (min:
+// all ones, max: zero) for the next ordering, in one launch.
+__global__ void __launch_bounds__(256) order_init_kernel(uint32_t* counts, uint32_t* box) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint32_t i = t; i < kOrderCells; i += gridDim.x * blockDim.x) counts[i] = 0u;
+  if (t < 6) box[t] = t < 3 ? 0xffffffffu : 0u;
 }
 
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* counts) {
@@ -125,10 +134,7 @@ cudaError_t launch_order_pack(SceneImpl& s, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
   uint32_t* counts = s.cells;
   uint32_t* box = s.cells + kOrderCells;
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * kOrderCells, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(box, 0xff, sizeof(uint32_t) * 3, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(box + 3, 0, sizeof(uint32_t) * 3, st);
-  if (e != cudaSuccess) return e;
+  order_init_kernel<<<32, 256, 0, st>>>(counts, box);
   box_kernel<<<grid_for(P, 2048, s.num_sms), 256, 0, st>>>(s.raw_points, P, box);
   cell_kernel<<<grid_for(P, 256, s.num_sms), 256, 0, st>>>(s.raw_points, P, box, s.cell, counts);
   scan_kernel<<<1, 1024, 0, st>>>(counts);
