@@ -164,9 +164,10 @@ __device__ __forceinline__ void fill_rcp_table(float* rcp, int t, int nthreads) 
 // groups of four global indices that meet [b, e), computes each group's
 // Philox block once, and samples its (up to four) bins of the range. Interior
 // groups of an aligned part load and store four bins at a time.
-// DEFER: bins with lambda >= 30 get kDeferredCount instead of their count (a
-// second pass, noise_deferred_warp, samples them), so the first pass holds no
-// out-of-line call and keeps its registers for the common bins.
+// DEFER: bins with lambda >= 30 get kDeferredCount instead of their count and
+// are listed (DeferList); a second pass samples them (noise_deferred_bin for
+// the dense list, noise_deferred_warp for overflowed regions), so the first
+// pass holds no out-of-line call and keeps its registers for the common bins.
 constexpr uint32_t kDeferredCount = 0xFFFFFFFFu;
 
 // Where DEFER puts the deferred bins: a dense list of their local indices
