@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import tempfile
@@ -507,7 +508,7 @@ def run_ours(args):
         # (a saturating leg: throughput at full load, latency dominated by queueing)
         line["serving_saturated"] = serving_bench(args.saturate_requests, args.saturate_rate)
     if rank == 0 and ws == 1 and args.lct_steps > 0:
-        line["lct"] = lct_bench(args.lct_steps)
+        line["lct"] = lct_bench(args.lct_steps, peaks)
     if rank == 0 and ws == 1 and args.occlusion_steps > 0:
         line["occlusion"] = occlusion_bench(args.occlusion_steps)
     if rank == 0:
@@ -558,11 +559,14 @@ def occlusion_bench(steps: int):
             "slowdown": out["with"] / out["without"]}
 
 
-def lct_bench(steps: int):
+def lct_bench(steps: int, peaks=None):
     """The paper's FFT forward model on its dataset shape (128 x 128 depth map,
     1024 bins of 32 ps, 2 m wall) against the direct pair sum of Eq. 1 on the
     same surface (one point per pixel at its depth-bin centre, no cosines,
-    window from the wall). Reports both times and the shape correlation."""
+    window from the wall). Reports both times, the shape correlation, and the
+    FFT model's FP64 roofline: two 3-D radix-2 transforms of the
+    (2N) x (2N) x (2M) volume V at 5 V log2(V) flops each, and the 6 V of the
+    spectral product, against the measured FP64 fma rate (2 flops each)."""
     import torch
     from paper_2506_03747_gb300 import nlos
     n, m, dt, w = 128, 1024, 32e-12, 1.0
@@ -611,11 +615,25 @@ def lct_bench(steps: int):
     sc.destroy()
     u, v = lct_tau.ravel().astype(np.float64), d_tau.ravel().astype(np.float64)
     corr = float(u @ v / (np.linalg.norm(u) * np.linalg.norm(v)))
-    return {"workload": "128 x 128 depth map (Gaussian bump on a tilted plane at 0.7-1.2 m), "
-                        "1024 bins x 32 ps, 2 m wall, Beta(2,2) albedo",
-            "grid": [2 * n, 2 * n, 2 * m], "lct_forward_ms": lct_ms,
-            "direct_forward_ms": direct_ms, "direct_pairs": n * n * n * n,
-            "shape_correlation_lct_vs_direct": corr}
+    out = {"workload": "128 x 128 depth map (Gaussian bump on a tilted plane at 0.7-1.2 m), "
+                       "1024 bins x 32 ps, 2 m wall, Beta(2,2) albedo",
+           "grid": [2 * n, 2 * n, 2 * m], "lct_forward_ms": lct_ms,
+           "direct_forward_ms": direct_ms, "direct_pairs": n * n * n * n,
+           "shape_correlation_lct_vs_direct": corr}
+    if peaks and peaks.get("dfma"):
+        vol = (2 * n) * (2 * n) * (2 * m)
+        flops = 2 * 5.0 * vol * math.log2(vol) + 6.0 * vol
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        peak = props.multi_processor_count * peaks["dfma"] * 2.0 * 2070e6
+        achieved = flops / (lct_ms * 1e-3)
+        out["lct_roofline"] = {
+            "bound": "fp64", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_basis": f"{props.multi_processor_count} SMs x {peaks['dfma']:.2f} FP64 fma "
+                          f"lanes/clk (measured) x 2 flops x 2070 MHz",
+            "work_basis": "two 3-D radix-2 FFTs of the (2N)^2 (2M) volume, 5 V log2 V flops "
+                          "each, and the spectral product (6 V)"}
+    return out
 
 
 def splat_moment_reds(params, pts, n_sample=128, seed=7):

@@ -445,6 +445,7 @@ typedef struct {
   double rmw_f32;             /* non-atomic shared load + add + store, all lanes */
   double red_f32_quarter;     /* red.shared.add.f32 with one lane in four active */
   double red_u32_quarter;     /* red.shared.add.u32 with one lane in four active */
+  double dfma;                /* FP64 fma (the FFT forward model's arithmetic) */
 } nlos_peaks;
 
 /* Runs the microbenchmarks on the current device (about a second; waits for

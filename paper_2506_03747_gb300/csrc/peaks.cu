@@ -19,7 +19,7 @@ enum PeakKind {
   PK_FFMA = 0,     // fmaf, 8 independent chains per thread
   PK_FFMA2,        // __ffma2_rn (two FMAs per lane and instruction)
   PK_SQRT,         // sqrt.approx.ftz.f32
-  PK_RCP,          // rcp.approx.ftz.f32
+  PK_RCP,          // rcp.approx.ftz.f32 (with one FP32 add a step)
   PK_RSQRT,        // rsqrt.approx.ftz.f32
   PK_LDS128,       // ld.shared.v4.f32, every lane the same address (broadcast)
   PK_RED_F32,      // red.shared.add.f32, all lanes
@@ -28,6 +28,7 @@ enum PeakKind {
   PK_RMW_F32,      // ld.shared + add + st.shared (no atomicity), all lanes
   PK_RED_F32_Q,    // red.shared.add.f32, one lane in four
   PK_RED_U32_Q,    // red.shared.add.u32, one lane in four
+  PK_DFMA,         // fma on doubles, 8 independent chains per thread
   PK_COUNT
 };
 
@@ -78,10 +79,12 @@ __global__ void __launch_bounds__(kPeakThreads, 1)
   for (int i = tid; i < kPeakRows * 32 * 2; i += blockDim.x) reinterpret_cast<float*>(smem)[i] = 0.f;
   float acc[kPeakChains];
   float2 acc2[kPeakChains];
+  double accd[K == PK_DFMA ? kPeakChains : 1];
 #pragma unroll
   for (int k = 0; k < kPeakChains; ++k) {
     acc[k] = seed + 0.001f * (float)(k + 1) + 1e-6f * (float)tid;
     acc2[k] = make_float2(acc[k], acc[k] + 0.5f);
+    if (K == PK_DFMA) accd[k] = (double)acc[k];
   }
   const float m = 0.999f, c = 1e-3f;
   __syncthreads();
@@ -92,6 +95,9 @@ __global__ void __launch_bounds__(kPeakThreads, 1)
     if (K == PK_FFMA) {
 #pragma unroll
       for (int k = 0; k < kPeakChains; ++k) acc[k] = fmaf(acc[k], m, c);
+    } else if (K == PK_DFMA) {
+#pragma unroll
+      for (int k = 0; k < kPeakChains; ++k) accd[k] = fma(accd[k], 0.999, 1e-3);
     } else if (K == PK_FFMA2) {
 #pragma unroll
       for (int k = 0; k < kPeakChains; ++k)
@@ -100,8 +106,9 @@ __global__ void __launch_bounds__(kPeakThreads, 1)
 #pragma unroll
       for (int k = 0; k < kPeakChains; ++k) acc[k] = mufu_sqrt(acc[k]);
     } else if (K == PK_RCP) {
+      // 1 / (1 + x): a chain the compiler cannot fold (1 / (1 / x) could be)
 #pragma unroll
-      for (int k = 0; k < kPeakChains; ++k) acc[k] = mufu_rcp(acc[k]);
+      for (int k = 0; k < kPeakChains; ++k) acc[k] = mufu_rcp(acc[k] + 1.0f);
     } else if (K == PK_RSQRT) {
 #pragma unroll
       for (int k = 0; k < kPeakChains; ++k) acc[k] = mufu_rsqrt(acc[k]);
@@ -155,6 +162,9 @@ __global__ void __launch_bounds__(kPeakThreads, 1)
   float s = 0.f;
 #pragma unroll
   for (int k = 0; k < kPeakChains; ++k) s += acc[k] + acc2[k].x + acc2[k].y;
+  if (K == PK_DFMA)
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) s += (float)accd[k];
   sink[(size_t)blockIdx.x * blockDim.x + tid] = s;
 }
 
@@ -166,7 +176,8 @@ constexpr double ops_per_iter(int k) {
 }
 
 constexpr int iters_of(int k) {
-  return (k == PK_FFMA || k == PK_FFMA2) ? 8192
+  return k == PK_DFMA ? 256
+         : (k == PK_FFMA || k == PK_FFMA2) ? 8192
          : (k == PK_SQRT || k == PK_RCP || k == PK_RSQRT || k == PK_LDS128) ? 1024
                                                                             : 256;
 }
@@ -225,7 +236,7 @@ extern "C" nlos_status nlos_measure_peaks(nlos_peaks* out, void* cuda_stream) {
   if (e == cudaSuccess) e = run_one<K>(n_sm, sink, cyc_dev, cyc, st, r[K]);
   NLOS_PK(PK_FFMA) NLOS_PK(PK_FFMA2) NLOS_PK(PK_SQRT) NLOS_PK(PK_RCP) NLOS_PK(PK_RSQRT)
   NLOS_PK(PK_LDS128) NLOS_PK(PK_RED_F32) NLOS_PK(PK_RED_U32) NLOS_PK(PK_RED_U64)
-  NLOS_PK(PK_RMW_F32) NLOS_PK(PK_RED_F32_Q) NLOS_PK(PK_RED_U32_Q)
+  NLOS_PK(PK_RMW_F32) NLOS_PK(PK_RED_F32_Q) NLOS_PK(PK_RED_U32_Q) NLOS_PK(PK_DFMA)
 #undef NLOS_PK
   cudaFreeAsync(sink, st);
   cudaFreeAsync(cyc_dev, st);
@@ -244,5 +255,6 @@ extern "C" nlos_status nlos_measure_peaks(nlos_peaks* out, void* cuda_stream) {
   out->rmw_f32 = r[PK_RMW_F32];
   out->red_f32_quarter = r[PK_RED_F32_Q];
   out->red_u32_quarter = r[PK_RED_U32_Q];
+  out->dfma = r[PK_DFMA];
   return NLOS_OK;
 }

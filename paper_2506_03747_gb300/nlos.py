@@ -81,7 +81,8 @@ class Peaks(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("num_sms", ctypes.c_int32)] + [
         (n, ctypes.c_double) for n in (
             "ffma", "ffma2", "sqrt_approx", "rcp_approx", "rsqrt_approx", "lds128_broadcast",
-            "red_f32", "red_u32", "red_u64", "rmw_f32", "red_f32_quarter", "red_u32_quarter")]
+            "red_f32", "red_u32", "red_u64", "rmw_f32", "red_f32_quarter", "red_u32_quarter",
+            "dfma")]
 
     def to_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "struct_size"}

@@ -266,3 +266,21 @@ def test_early_out_count():
     # every unit is ruled out from the bounds: no pair is touched
     assert g2["stats"]["pairs_full"] == 0 and g2["stats"]["pairs_tested"] == 0
     assert not g2["tau"].any()
+
+
+def test_measured_peaks_plausible():
+    """The roofline denominators of nlos_measure_peaks: every rate positive and
+    below the part's issue limits per SM clock (128 FP32 lanes, 16 MUFU lanes,
+    32 shared-memory lanes); FP64 fma below FP32; a shared reduction with a
+    quarter of the lanes active no faster per lane than four times a full one."""
+    H.lib()
+    from paper_2506_03747_gb300 import nlos
+    p = nlos.measure_peaks()
+    assert p["num_sms"] > 0
+    assert 0 < p["ffma"] <= 128.5 and 0 < p["ffma2"] <= 257
+    for k in ("sqrt_approx", "rcp_approx", "rsqrt_approx"):
+        assert 0 < p[k] <= 16.5
+    for k in ("red_f32", "red_u32", "red_u64", "rmw_f32", "red_f32_quarter", "red_u32_quarter"):
+        assert 0 < p[k] <= 32.5
+    assert 0 < p["dfma"] < p["ffma"]
+    assert p["red_f32_quarter"] <= 4 * p["red_f32"] * 1.05
