@@ -446,6 +446,7 @@ typedef struct {
   double red_f32_quarter;     /* red.shared.add.f32 with one lane in four active */
   double red_u32_quarter;     /* red.shared.add.u32 with one lane in four active */
   double dfma;                /* FP64 fma (the FFT forward model's arithmetic) */
+  double atom_f32;            /* atom.shared.add.f32 (old value returned), all lanes */
 } nlos_peaks;
 
 /* Runs the microbenchmarks on the current device (about a second; waits for

@@ -29,6 +29,7 @@ enum PeakKind {
   PK_RED_F32_Q,    // red.shared.add.f32, one lane in four
   PK_RED_U32_Q,    // red.shared.add.u32, one lane in four
   PK_DFMA,         // fma on doubles, 8 independent chains per thread
+  PK_ATOM_F32,     // atom.shared.add.f32 (old value returned), all lanes
   PK_COUNT
 };
 
@@ -131,6 +132,16 @@ __global__ void __launch_bounds__(kPeakThreads, 1)
                 addr[k]),
             "f"(acc[k]), "r"(on)
             : "memory");
+      }
+    } else if (K == PK_ATOM_F32) {
+#pragma unroll
+      for (int k = 0; k < kPeakChains; ++k) {
+        float old;
+        asm volatile("atom.shared.add.f32 %0, [%1], %2;"
+                     : "=f"(old)
+                     : "r"(addr[k]), "f"(acc[k])
+                     : "memory");
+        acc[k] += old * 0.0f;  // keeps the returned value live
       }
     } else if (K == PK_RED_U32 || K == PK_RED_U32_Q) {
 #pragma unroll
@@ -237,6 +248,7 @@ extern "C" nlos_status nlos_measure_peaks(nlos_peaks* out, void* cuda_stream) {
   NLOS_PK(PK_FFMA) NLOS_PK(PK_FFMA2) NLOS_PK(PK_SQRT) NLOS_PK(PK_RCP) NLOS_PK(PK_RSQRT)
   NLOS_PK(PK_LDS128) NLOS_PK(PK_RED_F32) NLOS_PK(PK_RED_U32) NLOS_PK(PK_RED_U64)
   NLOS_PK(PK_RMW_F32) NLOS_PK(PK_RED_F32_Q) NLOS_PK(PK_RED_U32_Q) NLOS_PK(PK_DFMA)
+  NLOS_PK(PK_ATOM_F32)
 #undef NLOS_PK
   cudaFreeAsync(sink, st);
   cudaFreeAsync(cyc_dev, st);
@@ -256,5 +268,6 @@ extern "C" nlos_status nlos_measure_peaks(nlos_peaks* out, void* cuda_stream) {
   out->red_f32_quarter = r[PK_RED_F32_Q];
   out->red_u32_quarter = r[PK_RED_U32_Q];
   out->dfma = r[PK_DFMA];
+  out->atom_f32 = r[PK_ATOM_F32];
   return NLOS_OK;
 }

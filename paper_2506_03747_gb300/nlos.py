@@ -82,7 +82,7 @@ class Peaks(ctypes.Structure):
         (n, ctypes.c_double) for n in (
             "ffma", "ffma2", "sqrt_approx", "rcp_approx", "rsqrt_approx", "lds128_broadcast",
             "red_f32", "red_u32", "red_u64", "rmw_f32", "red_f32_quarter", "red_u32_quarter",
-            "dfma")]
+            "dfma", "atom_f32")]
 
     def to_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "struct_size"}
