@@ -55,10 +55,32 @@ struct BwdArgs {
   float inv2s2, inv_s2, norm, reach, qstep;
 };
 
-// Leg factor F = cosf * wallf / r^2 and its delta-derivative (FP32).
-__device__ __forceinline__ void leg(int cos_mode, float ndotv, float vz, float nz, float r,
+#ifndef NLOS_BWD_RSQRT
+#define NLOS_BWD_RSQRT 1  // legs from a reciprocal square root estimate and one Newton step
+#endif
+
+// 1 / sqrt(x) for x > 0: the hardware estimate and one Newton step (about an
+// ulp; the gradients are held to 1e-3 of their maximum).
+__device__ __forceinline__ float rsqrt_newton(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y * fmaf(-0.5f * x, y * y, 1.5f);
+}
+
+// A leg's length and its reciprocal from its squared length.
+__device__ __forceinline__ void leg_length(float r2, float& r, float& ri) {
+#if NLOS_BWD_RSQRT
+  ri = rsqrt_newton(r2);
+  r = r2 * ri;
+#else
+  r = sqrtf(r2);
+  ri = 1.0f / r;
+#endif
+}
+
+// Leg factor F = cosf * wallf / r^2 and its delta-derivative (FP32); ri = 1 / r.
+__device__ __forceinline__ void leg(int cos_mode, float ndotv, float vz, float nz, float ri,
                                     float& F, float& dF, float& c) {
-  const float ri = 1.0f / r;
   c = -ndotv * ri;
   const float dc = -(1.0f - c * c) * ri;
   float fc = 1.0f, dfc = 0.0f;
@@ -167,9 +189,10 @@ __global__ void __launch_bounds__(256)
                 area = q[7];
     // laser leg l -> x and detector leg d -> x
     const float vlx = x - lx, vly = y - ly, vlz = z;
-    const float rl = sqrtf(vlx * vlx + vly * vly + vlz * vlz);
+    float rl, ril;
+    leg_length(vlx * vlx + vly * vly + vlz * vlz, rl, ril);
     float Fl, dFl, cl, Fd, dFd, cd, rd;
-    leg(a.cos_mode, nx * vlx + ny * vly + nz * vlz, vlz, nz, rl, Fl, dFl, cl);
+    leg(a.cos_mode, nx * vlx + ny * vly + nz * vlz, vlz, nz, ril, Fl, dFl, cl);
     if (a.scan_mode == NLOS_CONFOCAL) {
       // the laser spot is the detector spot: the second leg is the first
       rd = rl;
@@ -178,8 +201,9 @@ __global__ void __launch_bounds__(256)
       cd = cl;
     } else {
       const float vdx = x - dx_s, vdy = y - dy_s, vdz = z;
-      rd = sqrtf(vdx * vdx + vdy * vdy + vdz * vdz);
-      leg(a.cos_mode, nx * vdx + ny * vdy + nz * vdz, vdz, nz, rd, Fd, dFd, cd);
+      float rid;
+      leg_length(vdx * vdx + vdy * vdy + vdz * vdz, rd, rid);
+      leg(a.cos_mode, nx * vdx + ny * vdy + nz * vdz, vdz, nz, rid, Fd, dFd, cd);
     }
     const float qw = rho * area;
     const float w = qw * Fl * Fd;
