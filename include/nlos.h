@@ -240,7 +240,12 @@ nlos_status nlos_scene_shape(const nlos_scene* scene, uint64_t* num_scan, uint32
  *   stats      host, nullable: when given, the call waits for the stream and
  *              fills it.
  * Asynchronous on cuda_stream otherwise. Calls on one scene must not overlap
- * on the device (they share its scratch): use one stream per scene. */
+ * on the device (they share its scratch): use one stream per scene.
+ * Device memory: the forward's live-unit list (8 bytes a (tile, window, point
+ * block) unit) and the noise step's deferred-bin lists (about 3% of the bins)
+ * are stream-ordered allocations (cudaMallocAsync) freed on the same stream;
+ * the forward returns NLOS_ECUDA when its list cannot be allocated, the noise
+ * step falls back to one pass. */
 nlos_status nlos_simulate(nlos_scene* scene, float* tau_dev, uint32_t* counts_dev,
                           double* energy_dev, nlos_stats* stats, void* cuda_stream);
 
