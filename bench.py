@@ -905,6 +905,8 @@ def run_profile(args):
     from paper_2506_03747_gb300 import build as nbuild
     from paper_2506_03747_gb300 import nlos
     nbuild.build()
+    if args.profile == "glyph":
+        return _run_profile_glyph(args)
     params, pts_np = _workload(args.profile, 0)
     pts = torch.from_numpy(pts_np).cuda()
     sc = nlos.scene_create(nlos.params(params), pts)
@@ -919,6 +921,36 @@ def run_profile(args):
             nlos.scene_set_points(sc, pts)
             nlos.forward(sc, tau)
             nlos.detect(sc, tau, cnt, en)
+    torch.cuda.synchronize()
+    nlos.scene_check(sc)
+    sc.destroy()
+    return 0
+
+
+def _run_profile_glyph(args):
+    """Profile program of the differentiable path: one glyph scene of the
+    8-scene batch (64x64 scan, 65,536 points, 512 bins x 8 ps, splat with 60 ps
+    FWHM), each step the splat forward, the L2-loss gradient and the adjoint."""
+    import torch
+    import scenes
+    from paper_2506_03747_gb300 import nlos
+    params, sc_pts, tgt_pts = scenes.workload_glyph_batch(n_scenes=1)
+    prm = nlos.params(params)
+    sc = nlos.scene_create(prm, sc_pts[0])
+    tsc = nlos.scene_create(prm, tgt_pts[0])
+    S, B, P = sc.num_scan, sc.num_bins, sc.num_points
+    target = torch.empty((S, B), dtype=torch.float32, device="cuda")
+    nlos.simulate(tsc, target)
+    tsc.destroy()
+    tau = torch.empty_like(target)
+    g = torch.empty_like(target)
+    ga = torch.empty(P, dtype=torch.float32, device="cuda")
+    gd = torch.empty(P, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        nlos.forward(sc, tau)
+        torch.sub(tau, target, out=g)
+        g.mul_(2.0)
+        nlos.simulate_backward(sc, g, ga, gd)
     torch.cuda.synchronize()
     nlos.scene_check(sc)
     sc.destroy()
@@ -957,8 +989,9 @@ def main():
                     help="requests in the saturating serving leg (0: skip)")
     ap.add_argument("--saturate-rate", type=float, default=100000.0,
                     help="arrival rate of the saturating serving leg [1/s]")
-    ap.add_argument("--profile", choices=["heightfield128", "union64"], default=None,
-                    help="only run warmup + steps bench steps of this workload (for ncu)")
+    ap.add_argument("--profile", choices=["heightfield128", "union64", "glyph"], default=None,
+                    help="only run warmup + steps bench steps of this workload (for ncu; "
+                         "glyph: splat forward + adjoint of one configuration-4 scene)")
     ap.add_argument("--profile-forward", action="store_true",
                     help="with --profile: forward passes only")
     args = ap.parse_args()
