@@ -153,9 +153,11 @@ FORWARD_SOURCES = ("forward.cu", "forward_core.cuh", "device_util.cuh", "common.
 # cosine, its derivative and the 1/r^2 factor (18), 30 a leg; then the weight
 # and its two derivatives (8), u and du/d(delta) (4), the moment row and c (5),
 # two 6-term Horner evaluations and G1 (12), the two products (4), 33 in all.
-# A confocal scan has one leg (the laser spot is the detector spot): 63; a
-# non-confocal one two: 93 (a few of these are integer or select instructions).
-ADJ_FP32_SLOTS_PER_PAIR = {"confocal": 63, "nonconfocal": 93}
+# A pair evaluates one leg: a confocal scan's laser spot is its detector spot,
+# and a non-confocal scan's laser leg depends on the point only (the kernel
+# computes it once per point): 63 (a few of these are integer or select
+# instructions).
+ADJ_FP32_SLOTS_PER_PAIR = {"confocal": 63, "nonconfocal": 63}
 
 
 def launches_per_step(split: bool) -> int:

@@ -23,9 +23,13 @@
 //    so a first kernel correlates every transient of g with the 2N tables
 //    (2N floats per (s, j)) and the pair kernel needs one 48-byte gather and
 //    two Horner evaluations per pair instead of about 12 sigma taps.
-// In both, points are broadcast from shared memory, and a warp sum over the
+// Taps form: points are broadcast from shared memory, and a warp sum over the
 // 32 scan points of a tile gives the tile's contribution to each point, added
-// to the outputs with one global atomic.
+// to the outputs with one global atomic. Moments form: one thread per point,
+// looping over a block of scan points broadcast from shared memory; the sums
+// over s stay in the thread's registers (no warp sum), the laser leg of a
+// non-confocal scan is computed once per point, and each block of scan points
+// adds its contribution to each point with one global atomic.
 #include "common.cuh"
 #include "device_util.cuh"
 #include "forward_core.cuh"
@@ -38,6 +42,8 @@ namespace {
 
 constexpr int kBwdTile = 32;
 constexpr int kBwdPoints = 256;  // points per CTA
+constexpr int kBwdMomThreads = 256;  // moments form: points per CTA (one per thread)
+constexpr int kBwdMomScan = 128;     // moments form: scan points per CTA
 constexpr int kAdjTabThreads = 256;
 static_assert(kMoments == 6, "the adjoint table holds 2 x 6 moments in three float4");
 
@@ -153,25 +159,21 @@ __device__ __forceinline__ float horner6(float c, float p0, float p1, float p2, 
   return fmaf(fmaf(fmaf(fmaf(fmaf(p5, c, p4), c, p3), c, p2), c, p1), c, p0);
 }
 
-// MOM: T, J and rows of the moment tables (else unused).
-template <bool MOM>
-__global__ void __launch_bounds__(256)
-    bwd_kernel(const BwdArgs a, const float4* __restrict__ T, int J, uint32_t rows) {
+// Taps form: one CTA per (32-scan-point tile, block of kBwdPoints points).
+__global__ void __launch_bounds__(256) bwd_kernel(const BwdArgs a) {
   extern __shared__ float sm[];
-  float* gt = sm;                                           // [B][32] (taps form)
-  float* pts = sm + (MOM ? (size_t)0 : (size_t)a.B * kBwdTile);  // [kBwdPoints][8]
+  float* gt = sm;                              // [B][32]
+  float* pts = sm + (size_t)a.B * kBwdTile;    // [kBwdPoints][8]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const uint64_t n_pblk = (a.P + kBwdPoints - 1) / kBwdPoints;
   const uint64_t tile = blockIdx.x / n_pblk;
   const uint64_t p0 = (blockIdx.x % n_pblk) * kBwdPoints;
   const int np = (int)min((uint64_t)kBwdPoints, a.P - p0);
 
-  if (!MOM) {
-    for (uint32_t i = tid; i < a.B * kBwdTile; i += blockDim.x) {
-      const uint32_t s_loc = i & 31, b = i >> 5;
-      const uint64_t s = tile * kBwdTile + s_loc;
-      gt[i] = s < a.S ? a.g[s * a.B + b] : 0.0f;
-    }
+  for (uint32_t i = tid; i < a.B * kBwdTile; i += blockDim.x) {
+    const uint32_t s_loc = i & 31, b = i >> 5;
+    const uint64_t s = tile * kBwdTile + s_loc;
+    gt[i] = s < a.S ? a.g[s * a.B + b] : 0.0f;
   }
   for (int i = tid; i < np * 8; i += blockDim.x) pts[i] = a.raw[p0 * 8 + i];
   __syncthreads();
@@ -214,18 +216,7 @@ __global__ void __launch_bounds__(256)
     const float u = (rl + rd) * a.inv_cdt + sp.off;
     const float du_dd = -(cl + cd) * a.inv_cdt;
     float G0 = 0.f, G1 = 0.f;
-    if (MOM) {
-      const float fl = floorf(u);
-      if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f) && fl >= (float)-J &&
-          fl < (float)((int)rows - J)) {
-        const float c = 0.5f - (u - fl);
-        const float4* t = T + (s * rows + (uint64_t)((int)fl + J)) * 3;
-        const float4 t0 = __ldg(t), t1 = __ldg(t + 1), t2 = __ldg(t + 2);
-        G0 = horner6(c, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y);
-        const float gm = horner6(c, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w);
-        G1 = fmaf(c, G0, gm) * a.inv_s2;
-      }
-    } else if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f)) {
+    if (valid && (w != 0.f || dw_dd != 0.f || dw_drho != 0.f)) {
       const int lo = max(0, (int)(floorf(u - 0.5f - a.reach) + 1.0f));
       const int hi = min((int)a.B - 1, (int)(ceilf(u - 0.5f + a.reach) - 1.0f));
       if (lo <= hi) {
@@ -261,6 +252,88 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Moments form: thread = point p0 + threadIdx.x, CTA = (block of scan points,
+// block of points) with the scan block the slower index, so the CTAs resident
+// at one time read the moment tables of few transients. T[s][r] as written by
+// adj_table_kernel, rows = B + 2J.
+template <int SCAN, int COS>
+__global__ void __launch_bounds__(kBwdMomThreads)
+    bwd_mom_kernel(const BwdArgs a, const float4* __restrict__ T, int J, uint32_t rows,
+                   uint32_t n_pblk) {
+  __shared__ ScanPoint ss[kBwdMomScan];
+  const uint64_t s0 = (uint64_t)(blockIdx.x / n_pblk) * kBwdMomScan;
+  const uint64_t p = (uint64_t)(blockIdx.x % n_pblk) * kBwdMomThreads + threadIdx.x;
+  const int ns = (int)min((uint64_t)kBwdMomScan, a.S - s0);
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) ss[i] = a.scan[s0 + i];
+  __syncthreads();
+  if (p >= a.P) return;
+  const float4* rp = reinterpret_cast<const float4*>(a.raw + p * 8);
+  const float4 q0 = rp[0], q1 = rp[1];
+  const float x = q0.x, y = q0.y, z = q0.z, nx = q0.w, ny = q1.x, nz = q1.y, rho = q1.z,
+              area = q1.w;
+  const float z2 = z * z, nzz = nz * z, qw = rho * area;
+  // the laser leg of a non-confocal scan depends on the point only
+  float rl = 0.f, Fl = 0.f, dFl = 0.f, cl = 0.f;
+  if (SCAN != NLOS_CONFOCAL) {
+    const float vlx = x - a.lx, vly = y - a.ly;
+    float ril;
+    leg_length(fmaf(vlx, vlx, fmaf(vly, vly, z2)), rl, ril);
+    leg(COS, fmaf(nx, vlx, fmaf(ny, vly, nzz)), z, nz, ril, Fl, dFl, cl);
+  }
+  const float rows_hi = (float)((int)rows - J);
+  float ca = 0.f, cdl = 0.f;
+  for (int k = 0; k < ns; ++k) {
+    const ScanPoint sp = ss[k];
+    // the detector leg d -> x (for a confocal scan also the laser leg)
+    const float vdx = x - sp.sx, vdy = y - sp.sy;
+    float rd, rid, Fd, dFd, cd;
+    leg_length(fmaf(vdx, vdx, fmaf(vdy, vdy, z2)), rd, rid);
+    leg(COS, fmaf(nx, vdx, fmaf(ny, vdy, nzz)), z, nz, rid, Fd, dFd, cd);
+    float w, dw_drho, dw_dd, u, du_dd;
+    if (SCAN == NLOS_CONFOCAL) {
+      const float F2 = Fd * Fd;
+      w = qw * F2;
+      dw_drho = area * F2;
+      dw_dd = qw * 2.0f * Fd * dFd;
+      u = 2.0f * rd * a.inv_cdt + sp.off;
+      du_dd = -2.0f * cd * a.inv_cdt;
+    } else {
+      const float F2 = Fl * Fd;
+      w = qw * F2;
+      dw_drho = area * F2;
+      dw_dd = qw * (dFl * Fd + Fl * dFd);
+      u = (rl + rd) * a.inv_cdt + sp.off;
+      du_dd = -(cl + cd) * a.inv_cdt;
+    }
+    const float fl = floorf(u);
+    if ((w != 0.f || dw_dd != 0.f || dw_drho != 0.f) && fl >= (float)-J && fl < rows_hi) {
+      const float c = 0.5f - (u - fl);
+      const float4* t = T + ((s0 + (uint64_t)k) * rows + (uint64_t)((int)fl + J)) * 3;
+      const float4 t0 = __ldg(t), t1 = __ldg(t + 1), t2 = __ldg(t + 2);
+      const float G0 = horner6(c, t0.x, t0.y, t0.z, t0.w, t1.x, t1.y);
+      const float gm = horner6(c, t1.z, t1.w, t2.x, t2.y, t2.z, t2.w);
+      const float G1 = fmaf(c, G0, gm) * a.inv_s2;
+      ca = fmaf(dw_drho, G0, ca);
+      cdl = fmaf(dw_dd, G0, fmaf(w * du_dd, G1, cdl));
+    }
+  }
+  if (a.ga) atomicAdd(a.ga + p, ca);
+  if (a.gd) atomicAdd(a.gd + p, cdl);
+}
+
+using BwdMomFn = void (*)(const BwdArgs, const float4*, int, uint32_t, uint32_t);
+
+BwdMomFn pick_mom(int scan_mode, int cos_mode) {
+  if (scan_mode == NLOS_CONFOCAL) {
+    if (cos_mode == NLOS_COS_NONE) return bwd_mom_kernel<NLOS_CONFOCAL, NLOS_COS_NONE>;
+    if (cos_mode == NLOS_COS_OBJECT) return bwd_mom_kernel<NLOS_CONFOCAL, NLOS_COS_OBJECT>;
+    return bwd_mom_kernel<NLOS_CONFOCAL, NLOS_COS_OBJECT_WALL>;
+  }
+  if (cos_mode == NLOS_COS_NONE) return bwd_mom_kernel<NLOS_NONCONFOCAL, NLOS_COS_NONE>;
+  if (cos_mode == NLOS_COS_OBJECT) return bwd_mom_kernel<NLOS_NONCONFOCAL, NLOS_COS_OBJECT>;
+  return bwd_mom_kernel<NLOS_NONCONFOCAL, NLOS_COS_OBJECT_WALL>;
+}
+
 }  // namespace
 
 cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* grad_albedo,
@@ -292,8 +365,6 @@ cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* g
   a.norm = (float)(1.0 / (s * std::sqrt(2.0 * 3.14159265358979323846)));
   a.reach = (float)(6.0 * s);
   a.qstep = (float)std::exp(-1.0 / (s * s));
-  const uint64_t blocks = ((g.P + kBwdPoints - 1) / kBwdPoints) * ((g.S + kBwdTile - 1) / kBwdTile);
-  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
   if (use_moments(s)) {
     // moment tables: S x (B + 2J) x 48 bytes, stream-ordered, freed after use
     MomTab mt;
@@ -311,21 +382,28 @@ cudaError_t launch_backward(const SceneImpl& sc, const float* grad_tau, float* g
     adj_table_kernel<<<(unsigned)tab_blocks, kAdjTabThreads, 0, st>>>(t, mt);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
-      const size_t smem = sizeof(float) * kBwdPoints * 8;
-      bwd_kernel<true><<<(unsigned)blocks, 256, smem, st>>>(a, t.T, mt.J, t.rows);
-      e = cudaGetLastError();
+      const uint64_t n_pblk = (g.P + kBwdMomThreads - 1) / kBwdMomThreads;
+      const uint64_t mblocks = n_pblk * ((g.S + kBwdMomScan - 1) / kBwdMomScan);
+      if (mblocks > 0x7fffffffull) {
+        e = cudaErrorInvalidValue;
+      } else {
+        pick_mom(g.scan_mode, g.cos_mode)<<<(unsigned)mblocks, kBwdMomThreads, 0, st>>>(
+            a, t.T, mt.J, t.rows, (uint32_t)n_pblk);
+        e = cudaGetLastError();
+      }
     }
     const cudaError_t ef = cudaFreeAsync(t.T, st);
     return e != cudaSuccess ? e : ef;
   }
+  const uint64_t blocks = ((g.P + kBwdPoints - 1) / kBwdPoints) * ((g.S + kBwdTile - 1) / kBwdTile);
+  if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * ((size_t)g.B * kBwdTile + kBwdPoints * 8);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, sc.device);
   if (smem > (size_t)optin) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  e = cudaFuncSetAttribute(bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  bwd_kernel<false><<<(unsigned)blocks, 256, smem, st>>>(a, nullptr, 0, 0);
+  bwd_kernel<<<(unsigned)blocks, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
