@@ -273,7 +273,14 @@ nlos_status nlos_noise_part(nlos_scene* scene, const float* tau_dev, uint32_t* c
 /* Adjoint of the SPLAT forward (bin_mode must be SPLAT): given grad_tau_dev
  * = dL/dtau ([S][B] float32 device), writes dL/d albedo_p and dL/d delta_p
  * ([P] float32 device each, nullable), where delta_p displaces point p along
- * its normal (normal and area held fixed), evaluated at delta = 0. */
+ * its normal (normal and area held fixed), evaluated at delta = 0.
+ * grad_tau_dev must be 16-byte aligned. Asynchronous on cuda_stream; the
+ * outputs are zeroed, then accumulated with global atomics (the order of the
+ * FP32 additions, and so the last bits, may differ from call to call).
+ * Device memory: for a splat of sigma >= 2.5 bins (the moment form) a
+ * stream-ordered table of S x (B + 2J) x 48 bytes, J = ceil(6 sigma) + 1,
+ * allocated with cudaMallocAsync and freed on the same stream; NLOS_ECUDA
+ * when it cannot be allocated. */
 nlos_status nlos_simulate_backward(nlos_scene* scene, const float* grad_tau_dev,
                                    float* grad_albedo_dev, float* grad_depth_dev,
                                    void* cuda_stream);
